@@ -1,0 +1,294 @@
+"""Seeded synthetic graph generators.
+
+This module holds no arithmetic of the CMG method; it only builds inputs.  Both
+the CUDA path (tests, bench) and the CPU oracle consume the graphs it makes.
+Every graph is returned as a symmetric CSR triple ``(row_ptr int64[n+1],
+col int32[nnz], w float64[nnz])`` with ascending columns, no self-loops, no
+duplicate entries and strictly positive weights -- the input contract of
+``cmg_setup``.
+
+The paper measures on graphs of the University of Florida sparse matrix
+collection (Sec. 4, Table 2), which are not available here; the families below
+stand in for them: structured grids (the Table 3 / Sec. 3 model problem),
+Chung-Lu power-law graphs, random geometric graphs and Barabasi-Albert graphs.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = [
+    "csr_from_edges", "grid2d", "grid3d", "path", "cycle", "complete", "star",
+    "random_connected", "chung_lu", "rgg", "barabasi_albert", "largest_component",
+    "batch_graphs", "concat_csr", "serving_sizes",
+]
+
+
+def csr_from_edges(n: int, u, v, w):
+    """Symmetric CSR from an undirected edge list (u != v, no duplicate pairs)."""
+    u = np.asarray(u, dtype=np.int64)
+    v = np.asarray(v, dtype=np.int64)
+    w = np.asarray(w, dtype=np.float64)
+    if u.size and (np.any(u == v) or u.min() < 0 or v.min() < 0 or max(u.max(), v.max()) >= n):
+        raise ValueError("bad edge list")
+    rows = np.concatenate([u, v])
+    cols = np.concatenate([v, u])
+    ww = np.concatenate([w, w])
+    order = np.argsort(rows * n + cols, kind="stable")
+    rows = rows[order]
+    cols = cols[order].astype(np.int32)
+    ww = ww[order]
+    rp = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(rows, minlength=n), out=rp[1:])
+    return rp, cols, ww
+
+
+def _weights(m: int, weights, rng, lo=0.5, hi=1.5):
+    if weights == "unit":
+        return np.ones(m, dtype=np.float64)
+    if weights == "uniform":
+        return rng.uniform(lo, hi, size=m)
+    if weights == "lognormal":
+        return rng.lognormal(0.0, 1.0, size=m)
+    raise ValueError(weights)
+
+
+def grid2d(a: int, b: int, weights="unit", seed=1412):
+    """a x b 5-point grid.  Vertex (x, y) has id y*a + x.  Edge weights are
+    drawn in the order: all x-edges by id, then all y-edges by id."""
+    rng = np.random.default_rng(seed)
+    ids = np.arange(a * b, dtype=np.int64).reshape(b, a)
+    ex = (ids[:, :-1].ravel(), ids[:, 1:].ravel())
+    ey = (ids[:-1, :].ravel(), ids[1:, :].ravel())
+    u = np.concatenate([ex[0], ey[0]])
+    v = np.concatenate([ex[1], ey[1]])
+    return csr_from_edges(a * b, u, v, _weights(u.size, weights, rng))
+
+
+def grid3d(a: int, b: int, c: int, weights="uniform", seed=1412):
+    """a x b x c 7-point grid.  Vertex (x, y, z) has id (z*b + y)*a + x.  Edge
+    weights are drawn in the order: x-edges by id, y-edges by id, z-edges by id."""
+    rng = np.random.default_rng(seed)
+    ids = np.arange(a * b * c, dtype=np.int64).reshape(c, b, a)
+    ex = (ids[:, :, :-1].ravel(), ids[:, :, 1:].ravel())
+    ey = (ids[:, :-1, :].ravel(), ids[:, 1:, :].ravel())
+    ez = (ids[:-1, :, :].ravel(), ids[1:, :, :].ravel())
+    u = np.concatenate([ex[0], ey[0], ez[0]])
+    v = np.concatenate([ex[1], ey[1], ez[1]])
+    return csr_from_edges(a * b * c, u, v, _weights(u.size, weights, rng))
+
+
+def path(n: int, w=None):
+    """Path P_n; w (length n-1) gives the edge weights, default 1."""
+    u = np.arange(n - 1)
+    ww = np.ones(n - 1) if w is None else np.asarray(w, dtype=np.float64)
+    return csr_from_edges(n, u, u + 1, ww)
+
+
+def cycle(n: int, w=None):
+    u = np.arange(n)
+    v = (u + 1) % n
+    ww = np.ones(n) if w is None else np.asarray(w, dtype=np.float64)
+    return csr_from_edges(n, np.minimum(u, v), np.maximum(u, v), ww)
+
+
+def complete(n: int):
+    iu = np.triu_indices(n, 1)
+    return csr_from_edges(n, iu[0], iu[1], np.ones(iu[0].size))
+
+
+def star(n: int):
+    """Star with centre 0 and n-1 leaves."""
+    return csr_from_edges(n, np.zeros(n - 1, dtype=np.int64), np.arange(1, n), np.ones(n - 1))
+
+
+def random_connected(n: int, extra: int, seed: int, weights="uniform", ties=False):
+    """A random spanning tree plus `extra` random chords (duplicates merged).
+    ties=True draws weights from {1, 2, 3} so that many heaviest-edge ties occur."""
+    rng = np.random.default_rng(seed)
+    parent = np.array([rng.integers(0, i) for i in range(1, n)], dtype=np.int64)
+    u = np.concatenate([parent, rng.integers(0, n, size=extra)])
+    v = np.concatenate([np.arange(1, n), rng.integers(0, n, size=extra)])
+    keep = u != v
+    a, b = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    if ties:
+        ww = rng.integers(1, 4, size=a.size).astype(np.float64)
+    else:
+        ww = _weights(a.size, weights, rng)
+    return csr_from_edges(n, a, b, ww)
+
+
+def largest_component(n: int, u, v):
+    """Vertices of the largest connected component of an undirected edge list
+    (lowest-id component on ties), as a boolean mask."""
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    A = sp.coo_matrix((np.ones(len(u), dtype=np.int8), (u, v)), shape=(n, n)).tocsr()
+    ncomp, lab = connected_components(A, directed=False)
+    sizes = np.bincount(lab, minlength=ncomp)
+    return lab == int(np.argmax(sizes))
+
+
+def _relabel_keep(n, u, v, w, mask):
+    keep_e = mask[u] & mask[v]
+    newid = np.cumsum(mask) - 1
+    return int(mask.sum()), newid[u[keep_e]], newid[v[keep_e]], w[keep_e]
+
+
+def chung_lu(n: int = 4_194_304, mean_deg: float = 16.0, gamma: float = 2.5, seed: int = 1412,
+             weights="lognormal"):
+    """Chung-Lu power-law graph.  Expected degrees w_i proportional to
+    (i + 1)^(-1/(gamma-1)), scaled to mean `mean_deg` and capped at sqrt(n*mean_deg);
+    m = n*mean_deg/2 endpoint pairs drawn independently with probability
+    proportional to w; self-loops dropped, duplicates merged (one weight), the
+    largest connected component kept and relabelled in id order.  Weights are
+    lognormal(0, 1) per undirected edge (drawn after merging)."""
+    rng = np.random.default_rng(seed)
+    wt = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    wt *= mean_deg * n / wt.sum()
+    np.minimum(wt, np.sqrt(n * mean_deg), out=wt)
+    p = wt / wt.sum()
+    cdf = np.cumsum(p)
+    cdf[-1] = 1.0
+    m = int(n * mean_deg / 2)
+    u = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    v = np.searchsorted(cdf, rng.random(m), side="right").astype(np.int64)
+    np.minimum(u, n - 1, out=u)
+    np.minimum(v, n - 1, out=v)
+    keep = u != v
+    a, b = np.minimum(u[keep], v[keep]), np.maximum(u[keep], v[keep])
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    ww = _weights(a.size, weights, rng)
+    mask = largest_component(n, a, b)
+    n2, a, b, ww = _relabel_keep(n, a, b, ww, mask)
+    return csr_from_edges(n2, a, b, ww)
+
+
+def rgg(n: int, mean_deg: float = 8.0, seed: int = 1412, weights="uniform"):
+    """Random geometric graph: n points uniform in the unit square, an edge for
+    each pair closer than r = sqrt(mean_deg / (pi n)); the largest component is
+    kept.  Weights U[0.5, 1.5] per edge."""
+    rng = np.random.default_rng(seed)
+    pts = rng.random((n, 2))
+    r = np.sqrt(mean_deg / (np.pi * n))
+    ncell = max(1, int(1.0 / r))
+    cell = np.minimum((pts * ncell).astype(np.int64), ncell - 1)
+    cid = cell[:, 1] * ncell + cell[:, 0]
+    order = np.argsort(cid, kind="stable")
+    cstart = np.searchsorted(cid[order], np.arange(ncell * ncell + 1))
+    us, vs = [], []
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            ncx = cell[:, 0] + dx
+            ncy = cell[:, 1] + dy
+            ok = (ncx >= 0) & (ncx < ncell) & (ncy >= 0) & (ncy < ncell)
+            src = np.nonzero(ok)[0]
+            nc = ncy[src] * ncell + ncx[src]
+            cnt = cstart[nc + 1] - cstart[nc]
+            rep_src = np.repeat(src, cnt)
+            offs = np.arange(cnt.sum()) - np.repeat(np.cumsum(cnt) - cnt, cnt)
+            dst = order[np.repeat(cstart[nc], cnt) + offs]
+            sel = rep_src < dst
+            a, b = rep_src[sel], dst[sel]
+            d2 = ((pts[a] - pts[b]) ** 2).sum(axis=1)
+            close = d2 < r * r
+            us.append(a[close])
+            vs.append(b[close])
+    a = np.concatenate(us)
+    b = np.concatenate(vs)
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    ww = _weights(a.size, weights, rng)
+    mask = largest_component(n, a, b)
+    n2, a, b, ww = _relabel_keep(n, a, b, ww, mask)
+    return csr_from_edges(n2, a, b, ww)
+
+
+def barabasi_albert(n: int, m: int = 4, seed: int = 1412, weights="uniform"):
+    """Barabasi-Albert preferential attachment from an (m+1)-clique: vertex t
+    adds m edges whose far endpoints are copies of uniformly chosen earlier
+    edge endpoints (probability proportional to degree).  Repeated targets of
+    one vertex are merged into one edge."""
+    rng = np.random.default_rng(seed)
+    m0 = m + 1
+    iu = np.triu_indices(m0, 1)
+    e0 = iu[0].size
+    ne = e0 + (n - m0) * m
+    val = np.full(2 * ne, -1, dtype=np.int64)
+    val[0:2 * e0:2] = iu[0]
+    val[1:2 * e0:2] = iu[1]
+    ptr = np.arange(2 * ne, dtype=np.int64)
+    t = np.repeat(np.arange(m0, n, dtype=np.int64), m)
+    e = e0 + np.arange((n - m0) * m, dtype=np.int64)
+    val[2 * e] = t
+    avail = 2 * (e0 + (t - m0) * m)          # endpoints of edges made before vertex t
+    ptr[2 * e + 1] = np.floor(rng.random(e.size) * avail).astype(np.int64)
+    unresolved = val < 0
+    for _ in range(64):
+        if not unresolved.any():
+            break
+        ptr[unresolved] = ptr[ptr[unresolved]]
+        nv = val[ptr[unresolved]]
+        idx = np.nonzero(unresolved)[0]
+        val[idx] = nv
+        unresolved = val < 0
+    u = val[0::2]
+    v = val[1::2]
+    a, b = np.minimum(u, v), np.maximum(u, v)
+    key = np.unique(a * n + b)
+    a, b = key // n, key % n
+    return csr_from_edges(n, a, b, _weights(a.size, weights, rng))
+
+
+def concat_csr(graphs):
+    """Block-diagonal union of CSR graphs; returns (row_ptr, col, w, vertex_offsets)."""
+    offs = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, (rp, _, _) in enumerate(graphs):
+        offs[i + 1] = offs[i] + len(rp) - 1
+    nnz_offs = np.zeros(len(graphs) + 1, dtype=np.int64)
+    for i, (rp, _, _) in enumerate(graphs):
+        nnz_offs[i + 1] = nnz_offs[i] + rp[-1]
+    rp_all = np.empty(offs[-1] + 1, dtype=np.int64)
+    col_all = np.empty(nnz_offs[-1], dtype=np.int32)
+    w_all = np.empty(nnz_offs[-1], dtype=np.float64)
+    for i, (rp, col, w) in enumerate(graphs):
+        rp_all[offs[i]:offs[i + 1]] = rp[:-1] + nnz_offs[i]
+        col_all[nnz_offs[i]:nnz_offs[i + 1]] = col + offs[i]
+        w_all[nnz_offs[i]:nnz_offs[i + 1]] = w
+    rp_all[-1] = nnz_offs[-1]
+    return rp_all, col_all, w_all, offs
+
+
+def batch_graphs(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412):
+    """Mixed batch: sizes log-uniform in [lo, hi]; families round-robin
+    (random geometric graph with mean degree 8, near-square 2D grid, Barabasi-Albert
+    m=4); weights U[0.5, 1.5].  Returns a list of CSR triples."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
+    out = []
+    for i, nv in enumerate(sizes):
+        fam = i % 3
+        s = int(seed * 100003 + i)
+        if fam == 0:
+            out.append(rgg(int(nv), 8.0, seed=s))
+        elif fam == 1:
+            a = int(np.floor(np.sqrt(nv)))
+            out.append(grid2d(a, int(np.ceil(nv / a)), weights="uniform", seed=s))
+        else:
+            out.append(barabasi_albert(int(nv), 4, seed=s))
+    return out
+
+
+def serving_sizes(count: int, lo: float = 1e3, hi: float = 2e6, seed: int = 1412):
+    """Request sizes: log n ~ Normal truncated to [ln lo, ln hi], mean at the
+    midpoint, standard deviation (ln hi - ln lo) / 6."""
+    rng = np.random.default_rng(seed)
+    a, b = np.log(lo), np.log(hi)
+    mu, sd = 0.5 * (a + b), (b - a) / 6.0
+    out = []
+    while len(out) < count:
+        x = rng.normal(mu, sd, size=count)
+        out.extend(x[(x >= a) & (x <= b)].tolist())
+    return np.exp(np.array(out[:count])).astype(np.int64)

@@ -1,0 +1,446 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+The oracle (oracle/cmg_oracle.c) is the definition the CUDA path is compared
+with, so it is itself checked here against things other than itself:
+published generator outputs, closed-form spectra, invariants the paper proves
+(Lemma 2.2, Proposition 2.3, Theorem 2.4), hand-worked examples of Alg. 2,
+Table 3's level sizes, brute-force dense eigensolvers and library routines.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+from paper_1412_0565_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def dense_laplacian(rp, col, w):
+    n = len(rp) - 1
+    W = np.zeros((n, n))
+    for i in range(n):
+        W[i, col[rp[i]:rp[i + 1]]] = w[rp[i]:rp[i + 1]]
+    return np.diag(W.sum(axis=1)) - W
+
+
+def align(u, ref):
+    return u if np.dot(u, ref) >= 0 else -u
+
+
+def subspace_residual(u, Q):
+    Q, _ = np.linalg.qr(Q)
+    return np.linalg.norm(u - Q @ (Q.T @ u)) / np.linalg.norm(u)
+
+
+# ------------------------------------------------------------------ generators
+def test_splitmix64_published_outputs():
+    """SplitMix64 (Steele, Lea, Flood 2014): published reference outputs."""
+    G = 0x9E3779B97F4A7C15
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    for row in rows:
+        state = int(row[0], 0)
+        for k, out in enumerate(row[1:]):
+            assert oracle.splitmix64((state + k * G) & 0xFFFFFFFFFFFFFFFF) == int(out, 0)
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 16, 17, 63, 64, 65, 100, 255, 256, 1000, 4097])
+def test_visit_ranks_are_a_permutation(n):
+    """Alg. 2's randperm: the ranks must be a bijection onto [0, n)."""
+    for level in (0, 1, 5):
+        r = oracle.visit_ranks(1412, level, n)
+        assert sorted(r.tolist()) == list(range(n))
+
+
+def test_visit_ranks_depend_on_seed_and_level_and_look_random():
+    n = 20000
+    r0 = oracle.visit_ranks(1412, 0, n)
+    r1 = oracle.visit_ranks(1412, 1, n)
+    r2 = oracle.visit_ranks(7, 0, n)
+    assert (r0 != r1).mean() > 0.99 and (r0 != r2).mean() > 0.99
+    # rank correlation with the identity is O(1/sqrt(n)) for a random permutation
+    for r in (r0, r1, r2):
+        rho = np.corrcoef(np.arange(n), r)[0, 1]
+        assert abs(rho) < 5.0 / np.sqrt(n)
+
+
+def test_gaussian_start_is_standard_normal():
+    """Alg. 1 Step 2's randn: Box-Muller must give N(0, 1) samples."""
+    import scipy.stats as st
+    x = oracle.gaussian_start(1412, 200000)
+    assert abs(x.mean()) < 5.0 / np.sqrt(x.size)
+    assert abs(x.var() - 1.0) < 5.0 * np.sqrt(2.0 / x.size)
+    assert st.kstest(x, "norm").pvalue > 1e-4
+    y = oracle.gaussian_start(1413, 50)
+    assert not np.array_equal(y, x[:50])
+
+
+# ------------------------------------------------------------------ S1: argmax
+@pytest.mark.parametrize("seed", range(5))
+def test_heaviest_neighbour_brute_force(seed):
+    rp, col, w = inputs.random_connected(300, 600, seed=seed, ties=(seed % 2 == 0))
+    m = oracle.heaviest_neighbour(rp, col, w)
+    L = dense_laplacian(rp, col, w)
+    for v in range(len(rp) - 1):
+        colv = L[:, v].copy()
+        # argmin of the column of L; numpy returns the first (lowest) index
+        assert m[v] == int(np.argmin(colv))
+
+
+def test_heaviest_neighbour_pointer_graph_has_only_two_cycles():
+    """With lowest-index ties, following v -> m(v) never closes a cycle longer than 2."""
+    for seed in range(6):
+        rp, col, w = inputs.random_connected(400, 900, seed=seed, ties=True)
+        m = oracle.heaviest_neighbour(rp, col, w)
+        n = len(m)
+        for v in range(n):
+            x, seen = v, []
+            for _ in range(n + 1):
+                seen.append(x)
+                x = int(m[x])
+                if x in seen:
+                    cyc = seen[seen.index(x):]
+                    assert len(cyc) == 2
+                    break
+
+
+# ------------------------------------------------------------------ S2-S4: HEC
+def test_hec_hand_worked_path():
+    """Path 0-1-2-3 with weights 1, 3, 2: m = (1, 2, 1, 2).
+    Visit order 3, 0, 1, 2: vertex 3 creates {3, 2} as aggregate 0, vertex 0
+    creates {0, 1} as aggregate 1, vertices 1 and 2 are already mapped.
+    Visit order 1, 0, 3, 2: vertex 1 creates {1, 2}; 0 and 3 join it (c = 1)."""
+    rp, col, w = inputs.path(4, [1.0, 3.0, 2.0])
+    assert oracle.heaviest_neighbour(rp, col, w).tolist() == [1, 2, 1, 2]
+    agg, c = oracle.hec(rp, col, w, rank=[1, 2, 3, 0])
+    assert c == 2 and agg.tolist() == [1, 1, 0, 0]
+    agg, c = oracle.hec(rp, col, w, rank=[1, 0, 3, 2])
+    assert c == 1 and agg.tolist() == [0, 0, 0, 0]
+
+
+def test_hec_heavy_matching_is_order_independent():
+    """If the heaviest edges form a perfect matching, every visit order yields
+    exactly the matched pairs (Alg. 2 then coincides with heavy edge matching)."""
+    n = 40
+    wts = np.where(np.arange(n - 1) % 2 == 0, 3.0, 1.0)
+    rp, col, w = inputs.path(n, wts)
+    for s in range(10):
+        agg, c = oracle.hec(rp, col, w, oracle.visit_ranks(s, 0, n))
+        assert c == n // 2
+        for i in range(0, n, 2):
+            assert agg[i] == agg[i + 1]
+        assert len(set(agg.tolist())) == n // 2
+
+
+def test_hec_star_collapses_to_one_aggregate():
+    rp, col, w = inputs.star(30)
+    for s in range(8):
+        agg, c = oracle.hec(rp, col, w, oracle.visit_ranks(s, 0, 30))
+        assert c == 1 and (agg == 0).all()
+
+
+def _check_hec_invariants(rp, col, w, rank, agg, c):
+    n = len(rp) - 1
+    # labels are a surjection onto 0..c-1 (I^T 1 = 1: one aggregate per vertex)
+    assert agg.min() == 0 and agg.max() == c - 1
+    sizes = np.bincount(agg, minlength=c)
+    # Lemma 2.2: every aggregate has >= 2 vertices, so c <= n/2
+    assert sizes.min() >= 2 and c <= n // 2
+    # aggregates are numbered in the order their creators are visited
+    order = np.argsort(rank)
+    first_seen = []
+    seen = set()
+    for v in order:
+        a = int(agg[v])
+        if a not in seen:
+            seen.add(a)
+            first_seen.append(a)
+    assert first_seen == list(range(c))
+    # each aggregate is connected in the fine graph
+    import scipy.sparse as sp
+    from scipy.sparse.csgraph import connected_components
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    same = agg[rows] == agg[col]
+    A = sp.coo_matrix((np.ones(same.sum()), (rows[same], col[same])), shape=(n, n))
+    ncomp, _ = connected_components(A, directed=False)
+    assert ncomp == c
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_hec_invariants_random_graphs(seed):
+    rp, col, w = inputs.random_connected(500, 800, seed=seed, ties=(seed % 2 == 1))
+    rank = oracle.visit_ranks(seed, 0, 500)
+    agg, c = oracle.hec(rp, col, w, rank)
+    _check_hec_invariants(rp, col, w, rank, agg, c)
+
+
+def test_hec_invariants_grids():
+    for (a, b, wt) in [(30, 20, "unit"), (17, 23, "uniform")]:
+        rp, col, w = inputs.grid2d(a, b, wt, seed=3)
+        rank = oracle.visit_ranks(11, 0, a * b)
+        agg, c = oracle.hec(rp, col, w, rank)
+        _check_hec_invariants(rp, col, w, rank, agg, c)
+
+
+def test_level_sizes_match_table3():
+    """Table 3: the unit 100x100 grid coarsens as 10000, 3653, 1195, 384, 137,
+    46, 14.  The visit order is random, so the mean over seeds is compared
+    (within 10%, or 3 vertices on the two smallest levels where one vertex is
+    already 2-7%) on the levels the paper lists."""
+    with open(os.path.join(GOLDEN, "table3_level_sizes.txt")) as f:
+        paper = [int(x) for l in f if l.strip() and not l.startswith("#") for x in l.split()]
+    rp, col, w = inputs.grid2d(100, 100, "unit")
+    runs = [oracle.Hierarchy(rp, col, w, seed=s).sizes() for s in range(8)]
+    depth = min(len(r) for r in runs)
+    assert depth >= 6
+    for lvl in range(1, min(depth, len(paper))):
+        mean = np.mean([r[lvl] for r in runs])
+        assert abs(mean - paper[lvl]) <= max(0.10 * paper[lvl], 3.0), (lvl, mean, paper[lvl])
+    # the coarsest level is the first with <= 25 vertices (Alg. 1's while loop)
+    for r in runs:
+        assert r[-1] <= 25 and all(x > 25 for x in r[:-1])
+
+
+# ------------------------------------------------------------------ S5: Galerkin
+def _galerkin_check(rp, col, w, seed, exact):
+    h = oracle.Hierarchy(rp, col, w, seed=seed, coarse_size=2, max_levels=2)
+    assert h.levels == 2
+    agg = h.agg(0)
+    n, c = len(rp) - 1, h.info(1)[0]
+    rpc, colc, wc = h.csr(1)
+    L = dense_laplacian(rp, col, w)
+    P = np.zeros((c, n))
+    P[agg, np.arange(n)] = 1.0
+    Lc = P @ L @ P.T                      # explicit I L I^T
+    Wc = np.zeros((c, c))
+    for a in range(c):
+        Wc[a, colc[rpc[a]:rpc[a + 1]]] = wc[rpc[a]:rpc[a + 1]]
+        assert np.all(np.diff(colc[rpc[a]:rpc[a + 1]]) > 0)        # sorted, unique
+        assert a not in colc[rpc[a]:rpc[a + 1]]                     # no diagonal stored
+    assert np.array_equal(Wc, Wc.T)                                 # bitwise symmetric
+    assert np.all(wc > 0)                                           # off-diagonals of L_c < 0
+    off = -Lc.copy()
+    np.fill_diagonal(off, 0.0)
+    if exact:
+        assert np.array_equal(off, Wc)
+    else:
+        assert np.allclose(off, Wc, rtol=64 * np.finfo(float).eps, atol=0)
+    # Proposition 2.3(2): L_c 1 = 0, i.e. diag(L_c) = coarse row sums
+    assert np.allclose(np.diag(Lc), Wc.sum(axis=1), rtol=1e-13)
+    # Proposition 2.3(3): restriction keeps 1-perp
+    rng = np.random.default_rng(seed)
+    u = rng.standard_normal(n)
+    u -= u.mean()
+    assert abs((P @ u).sum()) <= 1e-12 * np.abs(u).sum()
+    # coarse graph is connected
+    from scipy.sparse.csgraph import connected_components
+    import scipy.sparse as sp
+    ncomp, _ = connected_components(sp.csr_matrix(Wc), directed=False)
+    assert ncomp == 1
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_galerkin_equals_triple_product_integer_weights(seed):
+    rp, col, w = inputs.random_connected(300, 700, seed=seed, ties=True)
+    _galerkin_check(rp, col, w, seed, exact=True)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_galerkin_equals_triple_product_real_weights(seed):
+    rp, col, w = inputs.random_connected(300, 700, seed=seed + 10)
+    _galerkin_check(rp, col, w, seed, exact=False)
+
+
+def test_galerkin_canonical_summation_order():
+    """R5: w_ab is the left-to-right sum over fine pairs in (i, j) order.  Weights
+    1, 2^-53, 2^-53 summed in that order give 1 (each tiny term rounds away); the
+    other orders would give 1 + 2^-52.  Fine graph: vertices 0,1 (aggregate A) and
+    2,3 (aggregate B) with heavy internal edges 0-1 and 2-3 and cross edges
+    0-2 (1), 0-3 (2^-53), 1-3 (2^-53)."""
+    t = 2.0 ** -53
+    u = [0, 2, 0, 0, 1]
+    v = [1, 3, 2, 3, 3]
+    ww = [10.0, 10.0, 1.0, t, t]
+    rp, col, w = inputs.csr_from_edges(4, u, v, ww)
+    h = oracle.Hierarchy(rp, col, w, seed=0, coarse_size=1, max_levels=2)
+    assert h.levels == 2 and h.info(1)[0] == 2
+    rpc, colc, wc = h.csr(1)
+    assert wc.tolist() == [1.0, 1.0]
+
+
+# ------------------------------------------------------------------ S9/S10: PI, RQ
+def test_rayleigh_residual_exact_eigenpair():
+    n = 30
+    rp, col, w = inputs.path(n)
+    i = np.arange(n)
+    phi = np.cos(np.pi * (i + 0.5) / n)
+    lam, res = oracle.rayleigh_residual(rp, col, w, phi)
+    assert abs(lam - (2 - 2 * np.cos(np.pi / n))) <= 1e-14
+    assert res <= 1e-14
+
+
+def test_gershgorin_shift():
+    rp, col, w = inputs.random_connected(100, 200, seed=1)
+    L = dense_laplacian(rp, col, w)
+    assert oracle.gershgorin(rp, col, w) == pytest.approx(np.abs(L).sum(axis=1).max(), rel=1e-15)
+
+
+def test_power_iteration_contraction_rate():
+    """Theorem 2.4 on B_g: the tangent of the angle to the Fiedler vector
+    contracts by (g - lambda3)/(g - lambda2) per sweep (path P_n)."""
+    n = 24
+    rp, col, w = inputs.path(n)
+    g = oracle.gershgorin(rp, col, w)
+    lam = 2 - 2 * np.cos(np.pi * np.arange(n) / n)
+    phi2 = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    phi2 /= np.linalg.norm(phi2)
+    y0 = oracle.gaussian_start(5, n)
+    tans = []
+    for k in (200, 260):
+        u, kk, _, _ = oracle.power_iteration(rp, col, w, y0, fixed=k)
+        c = abs(np.dot(u, phi2))
+        tans.append(np.sqrt(1 - c * c) / c)
+    rate = (tans[1] / tans[0]) ** (1.0 / 60)
+    assert rate == pytest.approx((g - lam[2]) / (g - lam[1]), rel=1e-2)
+
+
+def test_power_iteration_stops_on_cosine_rule():
+    rp, col, w = inputs.grid2d(12, 9, "uniform", seed=2)
+    y0 = oracle.gaussian_start(3, 108)
+    u, k, c, capped = oracle.power_iteration(rp, col, w, y0, tol=1e-8)
+    assert k >= 1 and c >= 1 - 1e-8 and not capped
+    # one sweep fewer would not have met the rule
+    u1, _, c1, _ = oracle.power_iteration(rp, col, w, y0, fixed=k - 1)
+    if k > 1:
+        assert c1 < 1 - 1e-8
+    # each iterate is orthogonal to 1 and normalised
+    assert abs(u.sum()) <= 1e-14 * np.sqrt(108)
+    assert abs(np.linalg.norm(u) - 1) <= 1e-14
+
+
+def test_two_vertex_graph():
+    """n = 2: the only vector orthogonal to 1 is (1, -1)/sqrt(2), lambda2 = 2w
+    (B_g annihilates it; the iteration stops on the eigenvector)."""
+    rp, col, w = inputs.path(2, [0.75])
+    u, lam, res, h, r = oracle.fiedler(rp, col, w)
+    assert h.levels == 1
+    assert np.allclose(u, [1 / np.sqrt(2), -1 / np.sqrt(2)], atol=1e-15)
+    assert lam == pytest.approx(1.5, rel=1e-15) and res <= 1e-15
+
+
+# ------------------------------------------------------------------ closed forms (converged mode)
+def _converged(rp, col, w, seed=1412):
+    # vector error ~ residual / (lambda3 - lambda2): drive the residual to 1e-14 g
+    u, lam, res, h, r = oracle.fiedler(rp, col, w, seed=seed, converged=True, conv_rtol=1e-14)
+    assert res <= 1e-14 * oracle.gershgorin(rp, col, w)
+    return u, lam, res
+
+
+def test_closed_form_path():
+    n = 40
+    rp, col, w = inputs.path(n)
+    u, lam, res = _converged(rp, col, w)
+    phi = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    phi /= np.linalg.norm(phi)
+    assert lam == pytest.approx(2 - 2 * np.cos(np.pi / n), rel=1e-12)
+    assert np.linalg.norm(align(u, phi) - phi) <= 1e-9
+
+
+def test_closed_form_cycle_double_eigenvalue():
+    n = 30
+    rp, col, w = inputs.cycle(n)
+    u, lam, res = _converged(rp, col, w)
+    i = np.arange(n)
+    Q = np.stack([np.cos(2 * np.pi * i / n), np.sin(2 * np.pi * i / n)], axis=1)
+    assert lam == pytest.approx(2 - 2 * np.cos(2 * np.pi / n), rel=1e-12)
+    assert subspace_residual(u, Q) <= 1e-9
+
+
+def test_closed_form_rectangular_grid():
+    a, b = 14, 9
+    rp, col, w = inputs.grid2d(a, b, "unit")
+    u, lam, res = _converged(rp, col, w)
+    x = np.tile(np.arange(a), b)
+    phi = np.cos(np.pi * (x + 0.5) / a)
+    phi /= np.linalg.norm(phi)
+    assert lam == pytest.approx(2 - 2 * np.cos(np.pi / a), rel=1e-12)
+    assert np.linalg.norm(align(u, phi) - phi) <= 1e-9
+
+
+def test_closed_form_square_grid_double_eigenvalue():
+    a = 12
+    rp, col, w = inputs.grid2d(a, a, "unit")
+    u, lam, res = _converged(rp, col, w)
+    x = np.tile(np.arange(a), a)
+    y = np.repeat(np.arange(a), a)
+    Q = np.stack([np.cos(np.pi * (x + 0.5) / a), np.cos(np.pi * (y + 0.5) / a)], axis=1)
+    assert lam == pytest.approx(2 - 2 * np.cos(np.pi / a), rel=1e-12)
+    assert subspace_residual(u, Q) <= 1e-9
+
+
+def test_closed_form_complete_and_star():
+    rp, col, w = inputs.complete(12)
+    u, lam, res = _converged(rp, col, w)
+    assert lam == pytest.approx(12.0, rel=1e-12) and abs(u.sum()) < 1e-13
+    rp, col, w = inputs.star(15)
+    u, lam, res = _converged(rp, col, w)
+    assert lam == pytest.approx(1.0, rel=1e-12)
+    assert abs(u[0]) < 1e-9 and abs(u.sum()) < 1e-13   # the centre is a node of every lambda=1 vector
+
+
+def test_weighted_path_against_tridiagonal_solver():
+    rng = np.random.default_rng(7)
+    n = 60
+    wts = rng.uniform(0.5, 1.5, n - 1)
+    rp, col, w = inputs.path(n, wts)
+    d = np.zeros(n)
+    d[:-1] += wts
+    d[1:] += wts
+    ev, V = sla.eigh_tridiagonal(d, -wts)
+    u, lam, res = _converged(rp, col, w)
+    assert lam == pytest.approx(ev[1], rel=1e-12)
+    assert np.linalg.norm(align(u, V[:, 1]) - V[:, 1]) <= 1e-9
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_random_graphs_against_dense_eigensolver(seed):
+    n = [40, 90, 150, 200][seed]
+    rp, col, w = inputs.random_connected(n, 2 * n, seed=100 + seed)
+    ev, V = np.linalg.eigh(dense_laplacian(rp, col, w))
+    u, lam, res = _converged(rp, col, w, seed=seed)
+    assert lam == pytest.approx(ev[1], rel=1e-12)
+    if (ev[2] - ev[1]) > 1e-3 * ev[1]:
+        assert np.linalg.norm(align(u, V[:, 1]) - V[:, 1]) <= 1e-8
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_cmg_default_mode_courant_fischer(seed):
+    """Default (tolerance) mode is approximate; it must still satisfy
+    lambda~ >= lambda2 (Courant-Fischer, u orthogonal to 1), be normalised,
+    orthogonal to 1, and carry the canonical sign."""
+    rp, col, w = inputs.random_connected(180, 400, seed=200 + seed)
+    ev = np.linalg.eigvalsh(dense_laplacian(rp, col, w))
+    g = oracle.gershgorin(rp, col, w)
+    u, lam, res, h, r = oracle.fiedler(rp, col, w, seed=seed)
+    assert lam >= ev[1] - 1e-14 * g
+    assert abs(np.linalg.norm(u) - 1) <= 1e-14
+    assert abs(u.sum()) <= 1e-14 * np.sqrt(len(u)) * 10
+    i = int(np.argmax(np.abs(u)))
+    assert u[i] > 0
+    assert (r["sweeps"] >= 1).all()
+
+
+def test_fixed_and_replay_schedules():
+    rp, col, w = inputs.grid2d(40, 30, "uniform", seed=5)
+    h = oracle.Hierarchy(rp, col, w, seed=9)
+    J = h.levels - 1
+    r = h.solve(schedule="fixed", beta=2.0, k0=3)
+    for j in range(J):
+        assert r["sweeps"][j] == int(np.ceil(3 * 2.0 ** j))
+    t = h.solve()
+    rr = h.solve(schedule="replay", replay=t["sweeps"])
+    assert np.array_equal(rr["sweeps"], t["sweeps"])
+    assert np.array_equal(rr["u"], t["u"])
