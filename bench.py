@@ -1,0 +1,334 @@
+"""Benchmark: CMG Fiedler solves/s on the 100^3 7-point grid (1M vertices).
+
+A step is one pass of the whole method (Alg. 1): cmg_setup (heavy edge
+coarsening + Galerkin products on every level) and cmg_fiedler (coarsest
+solve, prolongation and power iteration on every level, final vector,
+Rayleigh quotient and residual) on the synthetic 100x100x100 grid with
+U[0.5, 1.5] edge weights (seed 1412), inputs resident in device memory.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle (the
+plain sequential FP64 restatement of the method) on the same workload.
+With N > 1 ranks (torchrun), every rank solves its own replica of the
+workload (the method does not shard a single graph; replicas only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOAD = {"workload": "grid3d_100x100x100_uniform[0.5,1.5]_seed1412", "n": 1_000_000,
+            "edges": 2_970_000, "nnz": 5_940_000, "precision": "fp64", "tol": 1e-8,
+            "coarse_size": 25}
+METRIC = "Fiedler solves/s (CMG setup + solve, 3D grid 1M vertices, FP64)"
+UNIT = "solves/s"
+
+
+def make_graph():
+    from paper_1412_0565_gb300 import inputs
+    return inputs.grid3d(100, 100, 100, "uniform", seed=1412)
+
+
+def sweep_bytes(n, nnz, fp32=False):
+    """Algorithmic bytes of one power-iteration sweep: the CSR stream
+    (col int32 + weight), the row pointers, one read of x and one write of y."""
+    if fp32:
+        return 8 * nnz + 12 * n
+    return 12 * nnz + 20 * n
+
+
+def level_launch_bytes(n, nnz, sweeps, n_coarse, fp32=False):
+    """Algorithmic bytes of one power-iteration launch on a level: the start
+    vector (prolongation reads agg and the coarse vector, writes x; a second
+    pass re-reads x) plus `sweeps` sweeps."""
+    e = 4 if fp32 else 8
+    start = (4 * n + e * n_coarse + e * n) + e * n
+    return start + sweeps * sweep_bytes(n, nnz, fp32)
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax = float(p[1])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for l in f:
+                if l.lower().startswith(("model name", "cpu model")):
+                    model = l.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return model or os.uname().machine
+
+
+def oracle_solve(rp, col, w):
+    import oracle
+    h = oracle.Hierarchy(rp, col, w, seed=1412)
+    r = h.solve()
+    return r
+
+
+def run_reference(args):
+    """Reference arm: the CPU oracle (single thread) on the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    rp, col, w = make_graph()
+    for _ in range(args.warmup):
+        oracle_solve(rp, col, w)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle_solve(rp, col, w)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": dict(WORKLOAD, l2="input 71 MB < L2; CPU run"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"{args.steps} full CMG solves (setup+solve) of the 1M-vertex "
+                                   f"grid, single-threaded C oracle, {cpu_info()}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1412_0565_gb300 import cmg
+    cmg.load()
+    rp, col, w = make_graph()
+    n, nnz = len(rp) - 1, int(rp[-1])
+    drp = torch.from_numpy(rp).cuda()
+    dcol = torch.from_numpy(col).cuda()
+    dw = torch.from_numpy(w).cuda()
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    sid = stream.cuda_stream
+    opts = cmg.options(seed=1412, timing=1)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
+
+    def step():
+        h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
+        _, lam, st = h.fiedler(u_out=u, stream=sid)
+        h.close()
+        return lam, st
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    launches0 = cmg.kernel_launches()
+    step_ms, stats = [], []
+    barrier()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            lam, st = step()
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            stats.append(st)
+        barrier()
+    launches = cmg.kernel_launches() - launches0 - 0
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+
+    # ---- roofline of the dominant kernel: the power-iteration launches (k_power)
+    st0 = stats[-1]
+    ns, nnzs, sweeps = st0["n"], st0["nnz"], st0["sweeps"]
+    L = len(ns)
+    pi_bytes = 0
+    for j in range(L):
+        nc = ns[j + 1] if j + 1 < L else 0
+        pi_bytes += level_launch_bytes(ns[j], nnzs[j], sweeps[j], nc)
+    pi_ms = statistics.median(sum(s["level_ms"]) for s in stats)
+    lvl0_ms = statistics.median(s["level_ms"][0] for s in stats)
+    lvl0_bytes = level_launch_bytes(ns[0], nnzs[0], sweeps[0], ns[1] if L > 1 else 0)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if hbm_peak else "fallback"
+    if not hbm_peak:
+        hbm_peak = 6800.0
+    achieved0 = lvl0_bytes / (lvl0_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": "k_power (level 0 launch)", "achieved": achieved0,
+                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                "frac": achieved0 / hbm_peak, "traffic": None,
+                "bytes_per_launch": lvl0_bytes, "launch_ms": lvl0_ms,
+                "all_levels": {"bytes": pi_bytes, "ms": pi_ms,
+                               "achieved": pi_bytes / (pi_ms * 1e-3) / 1e9}}
+
+    # ---- end to end through the public API with host buffers
+    e2e_ms = []
+    hu = np.empty(n, dtype=np.float64)
+    rp_h = np.ascontiguousarray(rp)
+    for _ in range(max(2, min(args.steps, 5))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        h = cmg.Hierarchy(rp_h, col, w, seed=1412, stream=sid)
+        h.fiedler(u_out=hu, stream=sid)
+        h.close()
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e_val = world * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    if world > 1:
+        t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_val = world * len(e2e_ms) / (float(t.item()) / 1e3)
+
+    line = None
+    if rank == 0:
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            reps, t0 = 0, time.perf_counter()
+            while reps < 3 or (time.perf_counter() - t0 < 10 and reps < 8):
+                oracle_solve(rp, col, w)
+                reps += 1
+            dt = time.perf_counter() - t0
+            cpu = {"value": reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{reps} full CMG solves (setup+solve) of the same 1M-vertex grid, "
+                             f"single-threaded C oracle on {cpu_info()}"}
+        ms_sorted = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": dict(WORKLOAD, l2="256 MB buffer written between timed steps (flush)",
+                           parallelism=f"replicas{world}"),
+            "latency_ms": {"p50": ms_sorted[len(ms_sorted) // 2],
+                           "p99": ms_sorted[min(len(ms_sorted) - 1, int(0.99 * len(ms_sorted)))]},
+            "levels": {"n": ns, "nnz": nnzs, "sweeps": sweeps,
+                       "level_ms": [round(x, 4) for x in st0["level_ms"]]},
+            "lambda2": st0["lambda2"], "residual": st0["residual"],
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

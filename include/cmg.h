@@ -1,0 +1,229 @@
+/*
+ * cmg.h -- C-ABI of the GB300 cascadic multigrid (CMG) Fiedler-vector library.
+ *
+ * Method: J. C. Urschel, X. Hu, J. Xu, L. T. Zikatanov, "A cascadic multigrid
+ * algorithm for computing the Fiedler vector of graph Laplacians",
+ * arXiv 1412.0565.  The library computes an approximation of the Fiedler
+ * vector phi_2 and of the algebraic connectivity lambda_2 (Sec. 2,
+ * Definition 2.2) of a weighted undirected graph by Alg. 1: heavy edge
+ * coarsening (Alg. 2) with Galerkin coarse Laplacians L^{i+1} = I L I^T
+ * (Sec. 2 Step 1), power iteration on the coarsest graph from a Gaussian
+ * vector (Alg. 1 Step 2, Remark 2.3), then prolongation and power iteration
+ * (Alg. 3) on every finer level (Alg. 1 Step 3).
+ *
+ * Conventions shared by every entry point
+ *   - Graphs are CSR: row_ptr[n+1], col[nnz] (0-based), w[nnz].  The matrix is
+ *     the weighted adjacency matrix W of the graph; the Laplacian is
+ *     L = diag(W 1) - W (Definition 2.1).  The diagonal is never stored.
+ *   - Input contract (checked when options.validate != 0): n >= 2;
+ *     row_ptr[0] = 0, non-decreasing, row_ptr[n] = nnz < 2^31; every column
+ *     in [0, n), strictly ascending within a row (no duplicates), no
+ *     self-loop (Sec. 2: (i, i) is not an edge); every weight finite and > 0;
+ *     W symmetric with bitwise equal mirrored weights; no isolated vertex.
+ *     The graph is assumed connected (lambda_2 > 0); a disconnected graph is
+ *     processed but its result is a vector of the zero eigenspace.
+ *   - `mem` arguments say where a caller buffer lives: CMG_MEM_HOST or
+ *     CMG_MEM_DEVICE (a device pointer of the current CUDA device).
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *     stream-ordered; calls that return host values synchronise the stream.
+ *   - Input buffers are borrowed for the duration of the call and copied;
+ *     the library never keeps a caller pointer.  Output buffers are owned by
+ *     the caller and must have the stated length.
+ *   - Every call returns a cmg_status_t and never aborts the process.
+ */
+#ifndef CMG_H
+#define CMG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define CMG_MAX_LEVELS 64
+
+typedef enum cmg_status {
+    CMG_OK = 0,
+    CMG_WARN_MAXITER = 1,          /* a sweep cap stopped some level; result still usable */
+    CMG_ERR_INVALID_ARG = -1,      /* NULL pointer, bad enum, bad level index, ...        */
+    CMG_ERR_NOT_SYMMETRIC = -2,    /* a (i,j,w) without an identical (j,i,w)              */
+    CMG_ERR_SELF_LOOP = -3,
+    CMG_ERR_BAD_WEIGHT = -4,       /* weight <= 0, NaN or infinite                        */
+    CMG_ERR_ISOLATED_VERTEX = -5,
+    CMG_ERR_TOO_SMALL = -6,        /* n < 2                                               */
+    CMG_ERR_OOM = -7,              /* a device allocation failed                          */
+    CMG_ERR_CUDA = -8,             /* a CUDA runtime call failed                          */
+    CMG_ERR_DEVICE_TIMEOUT = -9,   /* a bounded device-side wait gave up                  */
+    CMG_ERR_BAD_CSR = -10,         /* row_ptr not monotone, column out of range,
+                                      columns not strictly ascending                      */
+    CMG_ERR_TOO_LARGE = -11        /* nnz >= 2^31 or a size beyond a stated limit         */
+} cmg_status_t;
+
+enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 };
+enum { CMG_PRECISION_FP64 = 0, CMG_PRECISION_FP32_SWEEP = 1 };
+enum { CMG_SCHEDULE_TOL = 0, CMG_SCHEDULE_FIXED = 1, CMG_SCHEDULE_REPLAY = 2 };
+
+/* Solver options.  cmg_options_default() fills the paper's settings. */
+typedef struct cmg_options {
+    double tol;        /* Alg. 3 stopping rule: stop when cos(u^k, u^{k-1}) >= 1 - tol
+                          (Sec. 2.2; Sec. 4 uses tol = 1e-8)                           */
+    double beta;       /* schedule FIXED: k_j = ceil(k0 * beta^j) sweeps on level j
+                          (Sec. 3, Theorem 3.10)                                        */
+    uint64_t seed;     /* keys the visit order of Alg. 2 and the Gaussian start of
+                          Alg. 1 Step 2                                                */
+    int32_t coarse_size;          /* Alg. 1: coarsen while n_i > coarse_size (25)      */
+    int32_t max_levels;           /* at most this many levels, 1..64 (64)              */
+    int32_t precision;            /* CMG_PRECISION_FP64 or CMG_PRECISION_FP32_SWEEP     */
+    int32_t schedule;             /* CMG_SCHEDULE_TOL / FIXED / REPLAY                  */
+    int32_t k0;                   /* schedule FIXED: sweeps on level 0                 */
+    int32_t max_sweeps;           /* sweep cap per level above the coarsest (20000)    */
+    int32_t max_sweeps_coarsest;  /* sweep cap on the coarsest level (100000)          */
+    int32_t validate;             /* 1: check the input contract in cmg_setup (1)      */
+    int32_t timing;               /* 1: cmg_fiedler times each level's power-iteration
+                                     launch with CUDA events (stats level_ms) (0)      */
+    int32_t reserved;             /* must be 0                                         */
+    int32_t replay_sweeps[CMG_MAX_LEVELS]; /* schedule REPLAY: exact sweeps on level j */
+} cmg_options_t;
+
+/* Per-solve report.  Level 0 is the input graph; level levels-1 the coarsest. */
+typedef struct cmg_stats {
+    double lambda2;    /* r = u^T L u for the returned unit vector u (Sec. 4)          */
+    double residual;   /* ||(L - r I) u||_2, the error metric of Sec. 4, Table 2       */
+    int32_t levels;    /* J + 1                                                        */
+    int32_t status;    /* CMG_OK or CMG_WARN_MAXITER                                   */
+    int64_t n[CMG_MAX_LEVELS];
+    int64_t nnz[CMG_MAX_LEVELS];
+    int32_t sweeps[CMG_MAX_LEVELS];      /* power-iteration sweeps k_j on level j      */
+    double cos_final[CMG_MAX_LEVELS];    /* cos(u^k, u^{k-1}) at the last sweep        */
+    double level_ms[CMG_MAX_LEVELS];     /* device time of level j's power-iteration
+                                            launch (options.timing; else 0)            */
+    double finalize_ms;                  /* device time of the final-vector launch     */
+} cmg_stats_t;
+
+typedef struct cmg_hierarchy_s *cmg_hierarchy_t;
+
+/* Fills *opts with tol = 1e-8, coarse_size = 25, max_levels = 64, seed = 1412,
+ * FP64, schedule TOL, beta = 4, k0 = 1, max_sweeps = 20000,
+ * max_sweeps_coarsest = 100000, validate = 1.  Errors: INVALID_ARG if NULL. */
+cmg_status_t cmg_options_default(cmg_options_t *opts);
+
+/* Static description of a status code (never NULL). */
+const char *cmg_status_string(cmg_status_t status);
+
+/* Library version string, e.g. "cmg-gb300 1.0 sm_103a". */
+const char *cmg_version(void);
+
+/*
+ * Setup phase, Alg. 1 Step 1 (Sec. 2.1): repeated heavy edge coarsening
+ * (Alg. 2) and Galerkin products L^{i+1} = I_i^{i+1} L^i (I_i^{i+1})^T while
+ * n_i > coarse_size; a level whose coarsening yields fewer than 2 aggregates
+ * becomes the coarsest.  The resulting hierarchy stays resident in device
+ * memory of the current device and is owned by the library until cmg_free.
+ *   n, row_ptr (int64[n+1]), col (int32[nnz]), w (double[nnz]): the graph,
+ *     in host or device memory according to `mem`.
+ *   opts: NULL means cmg_options_default().
+ *   out: receives the hierarchy handle (NULL on error).
+ * Errors: INVALID_ARG, TOO_SMALL, TOO_LARGE, BAD_CSR, SELF_LOOP, BAD_WEIGHT,
+ * NOT_SYMMETRIC, ISOLATED_VERTEX, OOM, CUDA, DEVICE_TIMEOUT.
+ */
+cmg_status_t cmg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w,
+                       int32_t mem, const cmg_options_t *opts, void *stream,
+                       cmg_hierarchy_t *out);
+
+/*
+ * Solve phase, Alg. 1 Steps 2-3: power iteration (Alg. 3) on the coarsest
+ * level from the Gaussian vector of Remark 2.3, then for j = J-1 .. 0
+ * prolongation y^(j) = (I_j^{j+1})^T y^(j+1), Gram-Schmidt against 1 (Sec. 2.2)
+ * and power iteration on B_g = g I - L^j with g = max_i sum_j |l_ij|.
+ *   u_out: double[n_0] in `u_mem` memory, or NULL; receives the unit vector,
+ *     orthogonal to 1, scaled so that its largest-magnitude entry (lowest
+ *     index on ties) is positive, in the caller's vertex order.
+ *   lambda2_out (host, nullable): r = u^T L u.
+ *   stats_out (host, nullable): per-level sizes, sweeps, cosines, residual.
+ * Returns OK, WARN_MAXITER (a cap was hit; outputs are valid), or an error
+ * (INVALID_ARG, OOM, CUDA, DEVICE_TIMEOUT).  Synchronises `stream`.
+ */
+cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double *lambda2_out,
+                         cmg_stats_t *stats_out, void *stream);
+
+/* Level count and per-level sizes (host arrays of length >= levels, nullable). */
+cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_per_level,
+                                int64_t *nnz_per_level);
+
+/* Device bytes held by the hierarchy (levels and solve workspace). */
+cmg_status_t cmg_hierarchy_device_bytes(cmg_hierarchy_t h, size_t *bytes);
+
+/* Upper estimate of the device bytes cmg_setup + cmg_fiedler hold for a graph
+ * of n vertices and nnz stored entries (used for admission control). */
+cmg_status_t cmg_estimate_device_bytes(int64_t n, int64_t nnz, int32_t precision, size_t *bytes);
+
+/* Aggregate map of level `level` onto level+1 (Alg. 2's q): host int32[n_level].
+ * Errors: INVALID_ARG if level is the coarsest or out of range. */
+cmg_status_t cmg_get_aggregates(cmg_hierarchy_t h, int32_t level, int32_t *agg_out);
+
+/* CSR of level `level` (off-diagonal weights; the diagonal is the row sum):
+ * host int64[n+1], int32[nnz], double[nnz]; any pointer may be NULL.
+ * Also returns the level's Gershgorin shift g through g_out (nullable). */
+cmg_status_t cmg_get_level_csr(cmg_hierarchy_t h, int32_t level, int64_t *row_ptr, int32_t *col,
+                               double *w, double *g_out);
+
+/* Releases the hierarchy (stream-ordered on the stream it was built on). */
+cmg_status_t cmg_free(cmg_hierarchy_t h);
+
+/* ------------------------------------------------------------------------
+ * Step entry points.  Each runs one step of the method on DEVICE buffers in
+ * the library's internal layout (row_ptr as int32[n+1]) on `stream`; they
+ * exist so every step can be checked on its own.  Inputs are assumed to meet
+ * the input contract (no validation).  Scratch memory is allocated and freed
+ * inside the call.
+ * ---------------------------------------------------------------------- */
+
+/* Alg. 2, "m <- argmin(L(:, v))": m_out[v] = the neighbour j of maximum w_vj,
+ * ties to the lowest j; -1 for a vertex without neighbours.  int32[n]. */
+cmg_status_t cmg_heaviest_neighbour(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                    const double *w, int32_t *m_out, void *stream);
+
+/* Alg. 2, "p <- randperm(n)", as visit ranks r(v) = p^{-1}(v): a 4-round
+ * Feistel permutation of [0, 2^k) keyed by splitmix64(seed ^ level*0x9E3779B97F4A7C15 ^ t),
+ * restricted to [0, n) by cycle walking.  rank_out: device uint32[n]. */
+cmg_status_t cmg_visit_ranks(int32_t n, uint64_t seed, int32_t level, uint32_t *rank_out,
+                             void *stream);
+
+/* Alg. 2 (heavy edge coarsening) for the visit ranks `rank` (device uint32[n],
+ * a permutation of [0, n)): agg_out (device int32[n]) receives q with labels
+ * 0..c-1 numbered in visit order; *c_out (host) receives c.  The result equals
+ * the sequential algorithm exactly.  Synchronises `stream`. */
+cmg_status_t cmg_hec_aggregate(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                               const double *w, const uint32_t *rank, int32_t *agg_out,
+                               int64_t *c_out, void *stream);
+
+/* Alg. 3 with a fixed sweep count: Gram-Schmidt of x_in against 1,
+ * normalisation, then exactly k sweeps u <- B_g u / ||B_g u|| (each followed
+ * by projection against 1), B_g = g I - L.  g <= 0 means "use
+ * max_i sum_j |l_ij|".  x_in, u_out: device double[n].  *cos_out (host,
+ * nullable): cosine between the last two iterates.  Synchronises `stream`. */
+cmg_status_t cmg_power_sweeps(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                              const double *w, double g, const double *x_in, int32_t k,
+                              double *u_out, double *cos_out, void *stream);
+
+/* Rayleigh quotient r = u^T L u / u^T u and residual ||(L - r I) u|| / ||u||
+ * (Sec. 4) of device double[n] u; results to host.  Synchronises `stream`. */
+cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                   const double *w, const double *u, double *lambda_out,
+                                   double *residual_out, void *stream);
+
+/* Number of kernel launches this library has issued in this process (all
+ * devices, all threads): lets a caller count the device work of a call. */
+cmg_status_t cmg_kernel_launches(uint64_t *count);
+
+/* Test hook for the error paths: the k-th next device allocation made by the
+ * library fails with CMG_ERR_OOM (k = 0: the next one; k < 0: disarm).  The
+ * paper has no counterpart; it exists so out-of-memory handling can be
+ * tested without exhausting the device. */
+cmg_status_t cmg_debug_fail_alloc_after(int64_t k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CMG_H */

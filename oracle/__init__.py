@@ -1,7 +1,7 @@
 """CPU oracle for the cascadic multigrid (CMG) Fiedler-vector method.
 
 TEST INFRASTRUCTURE ONLY.  A plain, sequential, FP64 restatement of
-arXiv 1412.0565 (Alg. 1, Alg. 2, Alg. 3; Definition 2.1; Proposition 2.3),
+arXiv 1412.0565 (Alg. 1, Alg. 2, Alg. 3; Definition 2.1; Proposition 2.7),
 written in C (``cmg_oracle.c``) and loaded here through ctypes.  Only the
 test-suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline /
 reference legs may import this package.  It shares no code with the CUDA

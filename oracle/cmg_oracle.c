@@ -15,7 +15,7 @@
  *   - heaviest neighbour m(v):  Alg. 2 (argmin of the column L(:,v))
  *   - visit order p = randperm: Alg. 2, restated as a keyed Feistel permutation
  *   - heavy edge coarsening:    Alg. 2, executed literally and sequentially
- *   - Galerkin coarse matrix:   Sec. 2 Step 1, L^{i+1} = I L I^T (Proposition 2.3)
+ *   - Galerkin coarse matrix:   Sec. 2 Step 1, L^{i+1} = I L I^T (Proposition 2.7)
  *   - power iteration:          Alg. 3 (projection against 1 as in Sec. 2.2)
  *   - cascade driver:           Alg. 1 (setup, coarsest solve, refinement)
  *   - error metric:             Sec. 4, ||(L - r I) y|| with r = y^T L y
@@ -37,11 +37,17 @@
  *       applied after every sweep (equal to Alg. 3 in exact arithmetic).
  *   R8  g = max_i (|l_ii| + sum_j |l_ij|) = max_i 2 d_i for a Laplacian.
  *   R9  lambda = (1/2) sum_i sum_j w_ij (u_i - u_j)^2 / ||u||^2.
- *   R10 if a sweep returns the zero vector after projection, the previous
- *       iterate is an eigenvector (lambda = g) and the iteration stops there.
+ *   R10 if a sweep returns, after projection, a vector of norm at most
+ *       64 eps g (rounding level; the iterate has norm 1), the previous
+ *       iterate is an eigenvector with B_g v = 0 (lambda = g, e.g. n = 2)
+ *       and the iteration stops there, keeping it.
  *   R11 the returned vector is scaled so that its largest-magnitude entry
  *       (lowest index on ties) is positive.
+ *   R12 a vertex without neighbours (possible on a coarse level of a
+ *       disconnected graph) has no heaviest neighbour and forms an aggregate
+ *       of its own when it is visited.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -172,7 +178,10 @@ ORC_EXPORT int64_t orc_hec(int64_t n, const int64_t *rp, const int32_t *col, con
         int64_t v = p[t];
         if (agg_out[v] != -1) continue;          /* already mapped: skip       */
         int32_t mv = m[v];
-        if (agg_out[mv] == -1) {                 /* heavy neighbour unmapped:  */
+        if (mv < 0) {                            /* R12: no neighbour at all   */
+            agg_out[v] = (int32_t)c;
+            c++;
+        } else if (agg_out[mv] == -1) {          /* heavy neighbour unmapped:  */
             agg_out[mv] = (int32_t)c;            /* new aggregate {v, m(v)}    */
             agg_out[v] = (int32_t)c;
             c++;
@@ -186,7 +195,7 @@ ORC_EXPORT int64_t orc_hec(int64_t n, const int64_t *rp, const int32_t *col, con
 }
 
 /* ------------------------------------------------------------------ */
-/* Galerkin product L^{i+1} = I L I^T (Sec. 2 Step 1; Proposition 2.3) with R5.
+/* Galerkin product L^{i+1} = I L I^T (Sec. 2 Step 1; Proposition 2.7) with R5.
  * The coarse graph is stored as CSR of the off-diagonal weights, columns
  * ascending; the diagonal (coarse degree) is implied by the row sums.         */
 typedef struct {
@@ -401,7 +410,7 @@ ORC_EXPORT int64_t orc_power_iteration(int64_t n, const int64_t *rp, const int32
         apply_bg(n, rp, col, w, d, g, v, u);
         double nrm = project_normalise(n, u);
         k++;
-        if (nrm == 0.0) { /* R10: v is an eigenvector with B_g v = 0 */
+        if (nrm <= 64.0 * DBL_EPSILON * g) { /* R10: v is an eigenvector with B_g v = 0 */
             memcpy(u, v, sizeof(double) * (size_t)n);
             c = 1.0;
             break;

@@ -1,0 +1,344 @@
+"""Thin ctypes binding of libcmg (the C-ABI in include/cmg.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+Host buffers are numpy arrays; device buffers are torch CUDA tensors (torch is
+used for device memory and streams, nothing else).  There is no CPU fallback:
+if the library cannot be loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+CMG_MAX_LEVELS = 64
+MEM_HOST, MEM_DEVICE = 0, 1
+FP64, FP32_SWEEP = 0, 1
+SCHEDULES = {"tol": 0, "fixed": 1, "replay": 2}
+
+STATUS = {
+    0: "OK", 1: "WARN_MAXITER", -1: "ERR_INVALID_ARG", -2: "ERR_NOT_SYMMETRIC",
+    -3: "ERR_SELF_LOOP", -4: "ERR_BAD_WEIGHT", -5: "ERR_ISOLATED_VERTEX", -6: "ERR_TOO_SMALL",
+    -7: "ERR_OOM", -8: "ERR_CUDA", -9: "ERR_DEVICE_TIMEOUT", -10: "ERR_BAD_CSR",
+    -11: "ERR_TOO_LARGE",
+}
+
+# every symbol include/cmg.h declares
+EXPORTS = [
+    "cmg_options_default", "cmg_status_string", "cmg_version", "cmg_setup", "cmg_fiedler",
+    "cmg_hierarchy_info", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
+    "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
+    "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
+    "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
+]
+
+
+class CmgError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        super().__init__(f"{what}: {self.name} ({status})" if what else f"{self.name} ({status})")
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double), ("beta", C.c_double), ("seed", C.c_uint64),
+        ("coarse_size", C.c_int32), ("max_levels", C.c_int32), ("precision", C.c_int32),
+        ("schedule", C.c_int32), ("k0", C.c_int32), ("max_sweeps", C.c_int32),
+        ("max_sweeps_coarsest", C.c_int32), ("validate", C.c_int32), ("timing", C.c_int32),
+        ("reserved", C.c_int32), ("replay_sweeps", C.c_int32 * CMG_MAX_LEVELS),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [
+        ("lambda2", C.c_double), ("residual", C.c_double), ("levels", C.c_int32),
+        ("status", C.c_int32), ("n", C.c_int64 * CMG_MAX_LEVELS),
+        ("nnz", C.c_int64 * CMG_MAX_LEVELS), ("sweeps", C.c_int32 * CMG_MAX_LEVELS),
+        ("cos_final", C.c_double * CMG_MAX_LEVELS), ("level_ms", C.c_double * CMG_MAX_LEVELS),
+        ("finalize_ms", C.c_double),
+    ]
+
+    def as_dict(self):
+        L = self.levels
+        return {"lambda2": self.lambda2, "residual": self.residual, "levels": L,
+                "status": STATUS.get(self.status, self.status),
+                "n": list(self.n[:L]), "nnz": list(self.nnz[:L]),
+                "sweeps": list(self.sweeps[:L]), "cos_final": list(self.cos_final[:L]),
+                "level_ms": list(self.level_ms[:L]), "finalize_ms": self.finalize_ms}
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_stale: bool = True):
+    """Loads libcmg.so (building it in-tree first when its sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build() if build_if_stale else _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libcmg.so not found at {path}; run __graft_entry__.build()")
+        lib = C.CDLL(path)
+        V = C.c_void_p
+        I32, I64, F64 = C.c_int32, C.c_int64, C.c_double
+        P = C.POINTER
+        sig = {
+            "cmg_options_default": (I32, [P(Options)]),
+            "cmg_status_string": (C.c_char_p, [I32]),
+            "cmg_version": (C.c_char_p, []),
+            "cmg_setup": (I32, [I64, V, V, V, I32, P(Options), V, P(V)]),
+            "cmg_fiedler": (I32, [V, V, I32, P(F64), P(Stats), V]),
+            "cmg_hierarchy_info": (I32, [V, P(I32), V, V]),
+            "cmg_hierarchy_device_bytes": (I32, [V, P(C.c_size_t)]),
+            "cmg_estimate_device_bytes": (I32, [I64, I64, I32, P(C.c_size_t)]),
+            "cmg_get_aggregates": (I32, [V, I32, V]),
+            "cmg_get_level_csr": (I32, [V, I32, V, V, V, P(F64)]),
+            "cmg_free": (I32, [V]),
+            "cmg_heaviest_neighbour": (I32, [I32, V, V, V, V, V]),
+            "cmg_visit_ranks": (I32, [I32, C.c_uint64, I32, V, V]),
+            "cmg_hec_aggregate": (I32, [I32, V, V, V, V, V, P(I64), V]),
+            "cmg_power_sweeps": (I32, [I32, V, V, V, F64, V, I32, V, P(F64), V]),
+            "cmg_rayleigh_residual": (I32, [I32, V, V, V, V, P(F64), P(F64), V]),
+            "cmg_kernel_launches": (I32, [P(C.c_uint64)]),
+            "cmg_debug_fail_alloc_after": (I32, [I64]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, what: str, allow_warn: bool = True):
+    if st == 0 or (allow_warn and st == 1):
+        return st
+    raise CmgError(st, what)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(int(stream))
+    try:
+        torch = _torch()
+        if torch.cuda.is_available():
+            return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return C.c_void_p(0)
+
+
+def _ptr(x):
+    """(pointer, mem) of a numpy array or torch tensor (contiguous)."""
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return C.c_void_p(x.ctypes.data), MEM_HOST
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return C.c_void_p(x.data_ptr()), (MEM_DEVICE if x.is_cuda else MEM_HOST)
+    raise TypeError(type(x))
+
+
+def options(**kw) -> Options:
+    o = Options()
+    _check(load().cmg_options_default(C.byref(o)), "cmg_options_default")
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": FP64, "fp32": FP32_SWEEP}[v]
+        if k == "schedule" and isinstance(v, str):
+            v = SCHEDULES[v]
+        if k == "replay_sweeps":
+            arr = (C.c_int32 * CMG_MAX_LEVELS)()
+            for i, x in enumerate(v):
+                arr[i] = int(x)
+            o.replay_sweeps = arr
+            continue
+        setattr(o, k, v)
+    return o
+
+
+def status_string(st: int) -> str:
+    return load().cmg_status_string(st).decode()
+
+
+def version() -> str:
+    return load().cmg_version().decode()
+
+
+def estimate_device_bytes(n: int, nnz: int, precision=FP64) -> int:
+    out = C.c_size_t()
+    _check(load().cmg_estimate_device_bytes(n, nnz, precision, C.byref(out)), "estimate")
+    return out.value
+
+
+def _as_inputs(row_ptr, col, w):
+    if isinstance(row_ptr, np.ndarray):
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        w = np.ascontiguousarray(w, dtype=np.float64)
+    return row_ptr, col, w
+
+
+class Hierarchy:
+    """Alg. 1 Step 1 (setup) resident on the GPU; `fiedler()` runs Steps 2-3."""
+
+    def __init__(self, row_ptr, col, w, *, opts: Options | None = None, stream=None, **kw):
+        lib = load()
+        if opts is None:
+            opts = options(**kw)
+        self.opts = opts
+        row_ptr, col, w = _as_inputs(row_ptr, col, w)
+        self._keep = (row_ptr, col, w)
+        p_rp, mem = _ptr(row_ptr)
+        p_col, mem2 = _ptr(col)
+        p_w, mem3 = _ptr(w)
+        if not (mem == mem2 == mem3):
+            raise ValueError("row_ptr, col and w must all be host or all be device buffers")
+        n = (row_ptr.shape[0] if hasattr(row_ptr, "shape") else len(row_ptr)) - 1
+        h = C.c_void_p()
+        self._h = None
+        st = lib.cmg_setup(n, p_rp, p_col, p_w, mem, C.byref(opts), _stream(stream), C.byref(h))
+        _check(st, "cmg_setup", allow_warn=False)
+        self._h = h
+        self._keep = None
+        self.n = n
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().cmg_free(self._h)
+            self._h = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def levels(self) -> int:
+        L = C.c_int32()
+        _check(load().cmg_hierarchy_info(self._h, C.byref(L), None, None), "info")
+        return L.value
+
+    def sizes(self):
+        L = self.levels
+        n = np.zeros(L, dtype=np.int64)
+        nnz = np.zeros(L, dtype=np.int64)
+        _check(load().cmg_hierarchy_info(self._h, None, C.c_void_p(n.ctypes.data),
+                                         C.c_void_p(nnz.ctypes.data)), "info")
+        return n.tolist(), nnz.tolist()
+
+    def device_bytes(self) -> int:
+        b = C.c_size_t()
+        _check(load().cmg_hierarchy_device_bytes(self._h, C.byref(b)), "bytes")
+        return b.value
+
+    def aggregates(self, level: int) -> np.ndarray:
+        n = self.sizes()[0][level]
+        a = np.empty(n, dtype=np.int32)
+        _check(load().cmg_get_aggregates(self._h, level, C.c_void_p(a.ctypes.data)), "aggregates")
+        return a
+
+    def level_csr(self, level: int):
+        ns, nnzs = self.sizes()
+        rp = np.empty(ns[level] + 1, dtype=np.int64)
+        col = np.empty(nnzs[level], dtype=np.int32)
+        w = np.empty(nnzs[level], dtype=np.float64)
+        g = C.c_double()
+        _check(load().cmg_get_level_csr(self._h, level, C.c_void_p(rp.ctypes.data),
+                                        C.c_void_p(col.ctypes.data), C.c_void_p(w.ctypes.data),
+                                        C.byref(g)), "level_csr")
+        return rp, col, w, g.value
+
+    def fiedler(self, u_out=None, stream=None):
+        """Returns (u, lambda2, stats dict).  u_out: numpy (host) or torch CUDA
+        tensor (device) of n float64; allocated on the host when None."""
+        if u_out is None:
+            u_out = np.empty(self.n, dtype=np.float64)
+        p_u, mem = _ptr(u_out)
+        lam = C.c_double()
+        stats = Stats()
+        st = load().cmg_fiedler(self._h, p_u, mem, C.byref(lam), C.byref(stats), _stream(stream))
+        _check(st, "cmg_fiedler")
+        return u_out, lam.value, stats.as_dict()
+
+
+def fiedler(row_ptr, col, w, *, stream=None, **kw):
+    """Alg. 1 end to end: setup + solve.  Returns (u, lambda2, stats)."""
+    with Hierarchy(row_ptr, col, w, stream=stream, **kw) as h:
+        return h.fiedler(stream=stream)
+
+
+# ------------------------------------------------------------------ step entry points
+def heaviest_neighbour(rp32, col, w, stream=None):
+    torch = _torch()
+    n = rp32.numel() - 1
+    m = torch.empty(n, dtype=torch.int32, device=rp32.device)
+    _check(load().cmg_heaviest_neighbour(n, _ptr(rp32)[0], _ptr(col)[0], _ptr(w)[0], _ptr(m)[0],
+                                         _stream(stream)), "heaviest_neighbour")
+    return m
+
+
+def visit_ranks(n: int, seed: int, level: int, device="cuda", stream=None):
+    torch = _torch()
+    r = torch.empty(n, dtype=torch.int32, device=device)
+    _check(load().cmg_visit_ranks(n, C.c_uint64(seed), level, _ptr(r)[0], _stream(stream)),
+           "visit_ranks")
+    return r
+
+
+def hec_aggregate(rp32, col, w, rank, stream=None):
+    torch = _torch()
+    n = rp32.numel() - 1
+    agg = torch.empty(n, dtype=torch.int32, device=rp32.device)
+    c = C.c_int64()
+    _check(load().cmg_hec_aggregate(n, _ptr(rp32)[0], _ptr(col)[0], _ptr(w)[0], _ptr(rank)[0],
+                                    _ptr(agg)[0], C.byref(c), _stream(stream)), "hec_aggregate")
+    return agg, c.value
+
+
+def power_sweeps(rp32, col, w, x_in, k: int, g: float = 0.0, stream=None):
+    torch = _torch()
+    n = rp32.numel() - 1
+    u = torch.empty(n, dtype=torch.float64, device=rp32.device)
+    cs = C.c_double()
+    _check(load().cmg_power_sweeps(n, _ptr(rp32)[0], _ptr(col)[0], _ptr(w)[0], float(g),
+                                   _ptr(x_in)[0], int(k), _ptr(u)[0], C.byref(cs), _stream(stream)),
+           "power_sweeps")
+    return u, cs.value
+
+
+def rayleigh_residual(rp32, col, w, u, stream=None):
+    lam = C.c_double()
+    res = C.c_double()
+    n = rp32.numel() - 1
+    _check(load().cmg_rayleigh_residual(n, _ptr(rp32)[0], _ptr(col)[0], _ptr(w)[0], _ptr(u)[0],
+                                        C.byref(lam), C.byref(res), _stream(stream)), "rayleigh")
+    return lam.value, res.value
+
+
+def kernel_launches() -> int:
+    c = C.c_uint64()
+    _check(load().cmg_kernel_launches(C.byref(c)), "kernel_launches")
+    return c.value
+
+
+def debug_fail_alloc_after(k: int):
+    load().cmg_debug_fail_alloc_after(int(k))

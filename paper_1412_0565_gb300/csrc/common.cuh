@@ -1,0 +1,201 @@
+// common.cuh -- internal helpers of libcmg (not part of the C-ABI).
+//
+// Error mapping, the library's stream-ordered device memory pool, a bounded
+// grid-wide barrier for cooperative persistent kernels, and warp/block
+// reductions with a fixed combination order (results are bitwise
+// reproducible from run to run).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/cmg.h"
+
+namespace cmg {
+
+// ----------------------------------------------------------------- errors
+cmg_status_t from_cuda(cudaError_t e);
+
+#define CMG_TRY(expr)                                                        \
+    do {                                                                     \
+        cmg_status_t _st = (expr);                                           \
+        if (_st != CMG_OK && _st != CMG_WARN_MAXITER) return _st;            \
+    } while (0)
+
+#define CMG_CUDA(expr)                                                       \
+    do {                                                                     \
+        cudaError_t _ce = (expr);                                            \
+        if (_ce != cudaSuccess) return ::cmg::from_cuda(_ce);                \
+    } while (0)
+
+// Status of the last kernel launch (launch-configuration errors only); also
+// counts the launch.  Every kernel launch of the library is followed by it.
+cmg_status_t launch_status();
+unsigned long long launches_issued();
+
+// ----------------------------------------------------------------- memory
+// Stream-ordered allocations from a library-owned pool on the current device.
+cmg_status_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+// Test hook: make the k-th next allocation fail with CMG_ERR_OOM (k < 0: off).
+void debug_fail_alloc_after(long long k);
+
+template <typename T>
+cmg_status_t dev_alloc_n(T **p, size_t count, cudaStream_t s) {
+    return dev_alloc(reinterpret_cast<void **>(p), count * sizeof(T), s);
+}
+
+// Frees every registered pointer (stream-ordered) when it goes out of scope.
+struct Scratch {
+    cudaStream_t stream;
+    std::vector<void *> ptrs;
+    explicit Scratch(cudaStream_t s) : stream(s) {}
+    ~Scratch() {
+        for (void *p : ptrs) dev_free(p, stream);
+    }
+    template <typename T>
+    cmg_status_t get(T **p, size_t count) {
+        cmg_status_t st = dev_alloc_n(p, count ? count : 1, stream);
+        if (st == CMG_OK) ptrs.push_back(*p);
+        return st;
+    }
+    Scratch(const Scratch &) = delete;
+    Scratch &operator=(const Scratch &) = delete;
+};
+
+// Device properties of the current device (cached).
+struct DeviceInfo {
+    int device;
+    int sms;
+    int max_smem_optin;
+};
+cmg_status_t device_info(DeviceInfo *out);
+
+// ----------------------------------------------------------------- grid barrier
+// State of one cooperative launch.  `count` and `gen` implement a sense-free
+// generation barrier; `err` records a barrier wait that ran out of time.
+struct GridSync {
+    unsigned int count;
+    unsigned int gen;
+    unsigned int err;
+    unsigned int pad;
+};
+
+// Nanoseconds since an arbitrary origin (device global timer).
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// A barrier wait gives up after this long and sets GridSync::err.
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+
+// Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every
+// thread of every CTA must call it.  Returns false (in every thread of the
+// CTA) when the barrier or an earlier one timed out; callers then return.
+__device__ __forceinline__ bool grid_sync(GridSync *gs) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (gridDim.x == 1) {
+        return true;
+    }
+    if (threadIdx.x == 0) {
+        volatile unsigned int *vgen = &gs->gen;
+        volatile unsigned int *verr = &gs->err;
+        unsigned int g0 = *vgen;
+        __threadfence();
+        unsigned int arrived = atomicAdd(&gs->count, 1u);
+        int ok = 1;
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&gs->count, 0u);
+            __threadfence();
+            atomicAdd(&gs->gen, 1u);
+        } else {
+            unsigned long long t0 = global_ns();
+            while (*vgen == g0) {
+                if (*verr) {
+                    ok = 0;
+                    break;
+                }
+                if (global_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicExch(&gs->err, 1u);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        if (*verr) ok = 0;
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ----------------------------------------------------------------- reductions
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over aligned groups of G lanes (G a power of two <= 32); every lane of
+// the warp must call it; all lanes of a group receive the group's sum.
+template <int G, typename T>
+__device__ __forceinline__ T group_sum(T v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-wide sum of K doubles per thread into out[0..K-1] of thread 0
+// (fixed order: lanes by xor-tree, then warps in index order).  `sm` must
+// hold 32*K doubles.  Contains __syncthreads.
+template <int K>
+__device__ __forceinline__ void block_sum(double (&v)[K], double *sm, double (&out)[K]) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int k = 0; k < K; k++) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) sm[warp * K + k] = v[k];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int k = 0; k < K; k++) {
+            double s = 0.0;
+            for (int i = 0; i < nw; i++) s += sm[i * K + k];
+            out[k] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ----------------------------------------------------------------- launch helpers
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Grid size for a plain grid-stride kernel: enough CTAs to cover `work`
+// items at `per_cta` items each, at most `waves` full waves of the GPU.
+int grid_for(long long work, int per_cta, int waves = 8);
+
+// Largest co-resident grid for a cooperative launch of `kernel`.
+cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out);
+
+// Launches `kernel` cooperatively with a zeroed GridSync at `gs`.
+cmg_status_t coop_launch(const void *kernel, int blocks, int threads, size_t smem,
+                         cudaStream_t s, void **args, GridSync *gs);
+
+}  // namespace cmg

@@ -1,0 +1,115 @@
+// internal.h -- host-side interfaces between the translation units of libcmg.
+#pragma once
+
+#include "common.cuh"
+
+namespace cmg {
+
+// Lanes per CSR row for a level of average row length `avg` (1..32, power of 2).
+int lanes_for_avg(double avg);
+
+// ---------------------------------------------------------------- hec.cu
+// Alg. 2 on one level: heaviest neighbours, visit ranks (Feistel keyed by
+// seed/level unless `rank` is given), round-based resolution and labelling.
+// agg_out: device int32[n].  *c_host receives the aggregate count.
+cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, const double *w,
+                       uint64_t seed, int level, const uint32_t *rank, int *agg_out, int *c_host,
+                       cudaStream_t s);
+// avg = average row length (chooses the lanes per row).
+cmg_status_t launch_heaviest(int n, double avg, const int *rp, const int *col, const double *w,
+                             int *m, cudaStream_t s);
+cmg_status_t launch_ranks(int n, uint64_t seed, int level, uint32_t *r, cudaStream_t s);
+
+// ---------------------------------------------------------------- primitives.cu
+// Exclusive scan of int32 in[0..n) into out[0..n]; out[n] = total (device).
+cmg_status_t exclusive_scan(const int *in, int *out, int n, Scratch &scr, cudaStream_t s);
+// Stable LSD radix sort of (key, val) by the low `bits` bits of key.  On
+// return *keys / *vals point at the sorted arrays (one of the two buffers).
+cmg_status_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
+                              uint32_t *vals_alt, int count, int bits, Scratch &scr,
+                              cudaStream_t s);
+
+// ---------------------------------------------------------------- galerkin.cu
+struct CoarseCSR {
+    int n;
+    long long nnz;
+    int *rp;
+    int *col;
+    double *w;
+    double g;
+};
+// Galerkin product I L I^T of the level (rp, col, w) with aggregate map agg
+// onto c aggregates; allocates the coarse CSR (caller frees with dev_free).
+cmg_status_t galerkin(int n, long long nnz, const int *rp, const int *col, const double *w,
+                      const int *agg, int c, CoarseCSR *out, cudaStream_t s);
+// Gershgorin shift g = max_i 2 * sum_j w_ij into *g_dev (device double).
+cmg_status_t launch_gershgorin(int n, const int *rp, const double *w, double *g_dev,
+                               cudaStream_t s);
+
+// ---------------------------------------------------------------- refine.cu
+// Result record of one power-iteration run (device memory).
+struct PiResult {
+    double mu;       // mean of the raw result buffer
+    double inv_s;    // 1 / ||raw - mu||
+    double cos;      // cosine between the last two iterates
+    double mu_prev;  // scalars of the previous iterate (used by the FP64 final sweep)
+    double inv_s_prev;
+    int buf;         // index (0/1) of the buffer that holds the raw result
+    int sweeps;
+    int capped;
+    int zero;        // R10: the last sweep produced the zero vector
+};
+
+struct PiLevel {
+    int n;
+    long long nnz;
+    const int *rp;
+    const int *col;
+    const double *w;     // FP64 weights
+    const float *w32;    // FP32 weights (FP32 sweep form) or nullptr
+    double g;
+    const int *agg;      // this level -> next coarser level (nullptr at the coarsest)
+    const int *tile_row; // row tiles of the sweep kernel (nullptr: built on demand)
+    int ntiles;
+};
+
+// Row tiles of a level for the tiled sweep kernel (tile_count + 1 entries).
+int tile_count(int n, long long nnz);
+cmg_status_t build_tiles(int n, long long nnz, const int *rp, int *tile_row, cudaStream_t s);
+
+// Power iteration (Alg. 3) on one level.  Start vector: x_init if given;
+// else, if coarse_res is given, the prolongation (I_j^{j+1})^T of the coarse
+// result held in coarse_buf / coarse_buf1 (whichever coarse_res->buf names);
+// else the Gaussian start of Alg. 1 Step 2 keyed by `seed`.
+// bufs: two vectors of n elements (double, or float when fp32).
+// mode 0: stop on the cosine rule or after max_sweeps; mode 1: exactly k_fixed sweeps.
+struct PiRun {
+    const PiLevel *lv;
+    int fp32;
+    int mode;
+    int k_fixed;
+    int max_sweeps;
+    double tol;
+    uint64_t seed;
+    const void *coarse_buf;
+    const void *coarse_buf1;
+    const PiResult *coarse_res;
+    const int *coarse_agg;           // agg of this level onto the coarse level
+    const double *x_init;
+    void *bufs[2];
+    PiResult *res;
+};
+cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s);
+
+// Level-0 finalisation in one cooperative launch:
+//   - unless `fresh`: u = (y - mu) / s from the result buffer (FP64 form), or,
+//     for the FP32 form, the last sweep recomputed in FP64 from the previous
+//     iterate and normalised;
+//   - if `sign`: scale u so that its largest-|u_i| entry (lowest index on
+//     ties) is positive;
+//   - out2[0] = u^T L u / u^T u, out2[1] = ||(L - out2[0] I) u|| / ||u||.
+cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void *buf1,
+                      const PiResult *res, double *u, int sign, int fresh, double *out2,
+                      GridSync *gs, cudaStream_t s);
+
+}  // namespace cmg

@@ -1,0 +1,138 @@
+// runtime.cu -- error mapping, the library's device memory pool, device
+// properties and cooperative-launch helpers.
+#include <atomic>
+#include <mutex>
+
+#include "internal.h"
+
+namespace cmg {
+
+cmg_status_t from_cuda(cudaError_t e) {
+    if (e == cudaSuccess) return CMG_OK;
+    cudaGetLastError();  // clear a non-sticky error so the context stays usable
+    if (e == cudaErrorMemoryAllocation) return CMG_ERR_OOM;
+    return CMG_ERR_CUDA;
+}
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}
+
+cmg_status_t launch_status() {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    return from_cuda(cudaGetLastError());
+}
+
+unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
+
+// ----------------------------------------------------------------- memory pool
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mutex;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+DeviceInfo g_info[kMaxDevices] = {};
+bool g_info_ok[kMaxDevices] = {};
+// test hook: the k-th next allocation fails (-1 = never)
+std::atomic<long long> g_fail_after{-1};
+
+cmg_status_t pool_for(int dev, cudaMemPool_t *out) {
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    if (dev < 0 || dev >= kMaxDevices) return CMG_ERR_CUDA;
+    if (!g_pool[dev]) {
+        cudaMemPoolProps props = {};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        CMG_CUDA(cudaMemPoolCreate(&p, &props));
+        // keep freed blocks cached in the pool between calls
+        uint64_t thr = ~0ull;
+        CMG_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &thr));
+        g_pool[dev] = p;
+    }
+    *out = g_pool[dev];
+    return CMG_OK;
+}
+}  // namespace
+
+cmg_status_t dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    long long f = g_fail_after.load();
+    if (f >= 0) {
+        if (f == 0) {
+            g_fail_after.store(-1);
+            return CMG_ERR_OOM;
+        }
+        g_fail_after.store(f - 1);
+    }
+    int dev = 0;
+    CMG_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    CMG_TRY(pool_for(dev, &pool));
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return from_cuda(e);
+    }
+    return CMG_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+void debug_fail_alloc_after(long long k) { g_fail_after.store(k); }
+
+cmg_status_t device_info(DeviceInfo *out) {
+    int dev = 0;
+    CMG_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return CMG_ERR_CUDA;
+    {
+        std::lock_guard<std::mutex> lk(g_pool_mutex);
+        if (g_info_ok[dev]) {
+            *out = g_info[dev];
+            return CMG_OK;
+        }
+    }
+    DeviceInfo d;
+    d.device = dev;
+    CMG_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
+    CMG_CUDA(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    std::lock_guard<std::mutex> lk(g_pool_mutex);
+    g_info[dev] = d;
+    g_info_ok[dev] = true;
+    *out = d;
+    return CMG_OK;
+}
+
+int grid_for(long long work, int per_cta, int waves) {
+    DeviceInfo d;
+    int sms = 148;
+    if (device_info(&d) == CMG_OK) sms = d.sms;
+    long long b = (work + per_cta - 1) / per_cta;
+    const long long cap = (long long)sms * 8 * waves;
+    if (b > cap) b = cap;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out) {
+    DeviceInfo d;
+    CMG_TRY(device_info(&d));
+    int per_sm = 0;
+    CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    if (per_sm < 1) return CMG_ERR_CUDA;
+    *out = per_sm * d.sms;
+    return CMG_OK;
+}
+
+cmg_status_t coop_launch(const void *kernel, int blocks, int threads, size_t smem,
+                         cudaStream_t s, void **args, GridSync *gs) {
+    CMG_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), s));
+    CMG_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(blocks), dim3(threads), args, smem, s));
+    return launch_status();
+}
+
+}  // namespace cmg

@@ -1,0 +1,76 @@
+"""The C-ABI library builds, loads and exports every symbol include/cmg.h
+declares; host-only entry points behave (no GPU needed)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1412_0565_gb300 import cmg
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "cmg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\s*\*?\s*(cmg_[a-z_0-9]+)\s*\(",
+                                 src, flags=re.M)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cmg.load()
+    names = declared_functions()
+    assert len(names) >= 17
+    assert sorted(names) == sorted(cmg.EXPORTS)
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_build_targets_sm_103a_only():
+    from paper_1412_0565_gb300 import build
+    assert build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_options_default_matches_paper_settings():
+    o = cmg.options()
+    assert o.tol == 1e-8 and o.coarse_size == 25 and o.max_levels == 64
+    assert o.precision == cmg.FP64 and o.schedule == 0 and o.validate == 1
+    assert C.sizeof(cmg.Options) == 320
+    assert C.sizeof(cmg.Stats) == 8 + 8 + 4 + 4 + 64 * (8 + 8 + 4 + 8 + 8) + 8
+
+
+def test_status_strings_and_version():
+    for code in cmg.STATUS:
+        assert cmg.status_string(code)
+    assert "sm_103a" in cmg.version()
+
+
+def test_host_side_argument_errors_need_no_gpu():
+    lib = cmg.load()
+    h = C.c_void_p()
+    rp = np.array([0, 0], dtype=np.int64)
+    col = np.zeros(1, dtype=np.int32)
+    w = np.ones(1)
+    st = lib.cmg_setup(1, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data),
+                       C.c_void_p(w.ctypes.data), 0, None, None, C.byref(h))
+    assert cmg.STATUS[st] == "ERR_TOO_SMALL"
+    st = lib.cmg_setup(5, None, None, None, 0, None, None, C.byref(h))
+    assert cmg.STATUS[st] == "ERR_INVALID_ARG"
+    st = lib.cmg_setup(5, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data),
+                       C.c_void_p(w.ctypes.data), 7, None, None, C.byref(h))
+    assert cmg.STATUS[st] == "ERR_INVALID_ARG"
+    bad = cmg.options(tol=2.0)
+    st = lib.cmg_setup(5, C.c_void_p(rp.ctypes.data), C.c_void_p(col.ctypes.data),
+                       C.c_void_p(w.ctypes.data), 0, C.byref(bad), None, C.byref(h))
+    assert cmg.STATUS[st] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_fiedler(None, None, 0, None, None, None)] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_free(None)] == "ERR_INVALID_ARG"
+
+
+def test_estimate_device_bytes_monotone():
+    a = cmg.estimate_device_bytes(1000, 6000)
+    b = cmg.estimate_device_bytes(1_000_000, 6_000_000)
+    assert 0 < a < b
+    assert cmg.estimate_device_bytes(10**6, 6 * 10**6, cmg.FP32_SWEEP) > 0
