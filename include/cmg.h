@@ -213,6 +213,32 @@ cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int3
                                    const double *w, const double *u, double *lambda_out,
                                    double *residual_out, void *stream);
 
+/* Limits of cmg_power_sweeps_noalloc. */
+#define CMG_NOALLOC_MAX_N 262144      /* rows    */
+#define CMG_NOALLOC_MAX_NNZ 4194304   /* entries */
+
+/* cmg_power_sweeps without any device memory allocation.  The paper has no
+ * counterpart; this entry point exists for callers that must not allocate:
+ * an application whose device memory is already fully reserved by its own
+ * allocator (a cudaMalloc from this library would fail or fragment that
+ * pool), or a latency-critical loop in which cudaMalloc / cudaFree, which may
+ * synchronise the device, are not allowed.  Same arguments, results and
+ * errors as cmg_power_sweeps, except:
+ *   - n <= CMG_NOALLOC_MAX_N and nnz <= CMG_NOALLOC_MAX_NNZ; larger graphs
+ *     are rejected with CMG_ERR_TOO_LARGE before any device work;
+ *   - its scratch is one fixed array of about 4.3 MB in device memory that
+ *     every GPU which loads this library holds until the process exits;
+ *   - the first call on a device looks up that array's device address
+ *     (cudaGetSymbolAddress) with the device current; make that first call
+ *     before any stream capture;
+ *   - all calls on a device share the array, so calls whose GPU work
+ *     overlaps (other streams, other host threads) race and give wrong
+ *     results: serialise them.  Each call clears what must start at zero.
+ * No cudaMalloc, cudaFree or allocating library routine is called. */
+cmg_status_t cmg_power_sweeps_noalloc(int32_t n, const int32_t *row_ptr, const int32_t *col,
+                                      const double *w, double g, const double *x_in, int32_t k,
+                                      double *u_out, double *cos_out, void *stream);
+
 /* Number of kernel launches this library has issued in this process (all
  * devices, all threads): lets a caller count the device work of a call. */
 cmg_status_t cmg_kernel_launches(uint64_t *count);

@@ -36,8 +36,11 @@ EXPORTS = [
     "cmg_hierarchy_info", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
     "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
     "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
-    "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
+    "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
 ]
+
+NOALLOC_MAX_N = 262144
+NOALLOC_MAX_NNZ = 4194304
 
 
 class CmgError(RuntimeError):
@@ -109,6 +112,7 @@ def load(build_if_stale: bool = True):
             "cmg_hec_aggregate": (I32, [I32, V, V, V, V, V, P(I64), V]),
             "cmg_power_sweeps": (I32, [I32, V, V, V, F64, V, I32, V, P(F64), V]),
             "cmg_rayleigh_residual": (I32, [I32, V, V, V, V, P(F64), P(F64), V]),
+            "cmg_power_sweeps_noalloc": (I32, [I32, V, V, V, F64, V, I32, V, P(F64), V]),
             "cmg_kernel_launches": (I32, [P(C.c_uint64)]),
             "cmg_debug_fail_alloc_after": (I32, [I64]),
         }
@@ -323,6 +327,20 @@ def power_sweeps(rp32, col, w, x_in, k: int, g: float = 0.0, stream=None):
                                    _ptr(x_in)[0], int(k), _ptr(u)[0], C.byref(cs), _stream(stream)),
            "power_sweeps")
     return u, cs.value
+
+
+def power_sweeps_noalloc(rp32, col, w, x_in, k: int, g: float = 0.0, u_out=None, stream=None):
+    """cmg_power_sweeps_noalloc: same as power_sweeps, scratch in a fixed device
+    array (no allocation by the library).  u_out: torch CUDA float64 tensor."""
+    torch = _torch()
+    n = rp32.numel() - 1
+    if u_out is None:
+        u_out = torch.empty(n, dtype=torch.float64, device=rp32.device)
+    cs = C.c_double()
+    _check(load().cmg_power_sweeps_noalloc(n, _ptr(rp32)[0], _ptr(col)[0], _ptr(w)[0], float(g),
+                                           _ptr(x_in)[0], int(k), _ptr(u_out)[0], C.byref(cs),
+                                           _stream(stream)), "power_sweeps_noalloc")
+    return u_out, cs.value
 
 
 def rayleigh_residual(rp32, col, w, u, stream=None):

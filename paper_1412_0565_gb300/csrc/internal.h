@@ -99,7 +99,18 @@ struct PiRun {
     void *bufs[2];
     PiResult *res;
 };
-cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s);
+// Caller-provided scratch for power_iteration / finalize (nullptr: the
+// functions allocate their own).  Capacities are in elements.
+struct PiWorkspace {
+    int *tile_row;
+    int tile_cap;
+    double *partials;
+    int partials_cap;
+    double *fin_part;
+    int fin_part_cap;
+};
+cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s,
+                             const PiWorkspace *ws = nullptr);
 
 // Level-0 finalisation in one cooperative launch:
 //   - unless `fresh`: u = (y - mu) / s from the result buffer (FP64 form), or,
@@ -110,6 +121,6 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s);
 //   - out2[0] = u^T L u / u^T u, out2[1] = ||(L - out2[0] I) u|| / ||u||.
 cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void *buf1,
                       const PiResult *res, double *u, int sign, int fresh, double *out2,
-                      GridSync *gs, cudaStream_t s);
+                      GridSync *gs, cudaStream_t s, const PiWorkspace *ws = nullptr);
 
 }  // namespace cmg

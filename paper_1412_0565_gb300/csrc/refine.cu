@@ -503,7 +503,7 @@ bool small_level_fits(int n, long long nnz, int fp32) {
     return b + 32 * kNumPartials * 8 + 256 <= (size_t)d.max_smem_optin;
 }
 
-cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s) {
+cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
     const PiLevel &lv = *run.lv;
     Scratch scr(s);
     PiArgs a;
@@ -541,7 +541,12 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s) {
     }
     if (!a.tile_row) {
         int *tr;
-        CMG_TRY(scr.get(&tr, (size_t)tile_count(lv.n, lv.nnz) + 1));
+        if (ws) {
+            if (tile_count(lv.n, lv.nnz) + 1 > ws->tile_cap) return CMG_ERR_TOO_LARGE;
+            tr = ws->tile_row;
+        } else {
+            CMG_TRY(scr.get(&tr, (size_t)tile_count(lv.n, lv.nnz) + 1));
+        }
         CMG_TRY(build_tiles(lv.n, lv.nnz, lv.rp, tr, s));
         a.tile_row = tr;
         a.ntiles = tile_count(lv.n, lv.nnz);
@@ -554,7 +559,12 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s) {
     // at least 4 tiles per CTA where possible, never more CTAs than co-resident
     int blocks = std::max(1, std::min(maxb, (a.ntiles + 3) / 4));
     double *partials;
-    CMG_TRY(scr.get(&partials, (size_t)2 * blocks * kNumPartials));
+    if (ws) {
+        if (2 * blocks * kNumPartials > ws->partials_cap) return CMG_ERR_TOO_LARGE;
+        partials = ws->partials;
+    } else {
+        CMG_TRY(scr.get(&partials, (size_t)2 * blocks * kNumPartials));
+    }
     a.partials = partials;
     return coop_launch(kern, blocks, kTileThreads, smem, s, args, gs);
 }
@@ -779,7 +789,7 @@ static const void *finalize_kernel(int G) {
 
 cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void *buf1,
                       const PiResult *res, double *u, int sign, int fresh, double *out2,
-                      GridSync *gs, cudaStream_t s) {
+                      GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
     const int G = lanes_for_avg((double)lv.nnz / (double)std::max(1, lv.n));
     const void *kern = finalize_kernel(G);
     int maxb = 0;
@@ -791,8 +801,13 @@ cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void 
     blocks = std::max(1, blocks);
     Scratch scr(s);
     double *part, *tmp = nullptr;
-    CMG_TRY(scr.get(&part, (size_t)12 * blocks));
-    if (fp32 && !fresh) CMG_TRY(scr.get(&tmp, (size_t)lv.n));
+    if (ws) {
+        if (12 * blocks > ws->fin_part_cap || (fp32 && !fresh)) return CMG_ERR_TOO_LARGE;
+        part = ws->fin_part;
+    } else {
+        CMG_TRY(scr.get(&part, (size_t)12 * blocks));
+        if (fp32 && !fresh) CMG_TRY(scr.get(&tmp, (size_t)lv.n));
+    }
     FinArgs a;
     a.n = lv.n;
     a.rp = lv.rp;
