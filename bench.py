@@ -31,7 +31,9 @@ if ROOT not in sys.path:
 WORKLOAD = {"workload": "grid3d_100x100x100_uniform[0.5,1.5]_seed1412", "n": 1_000_000,
             "edges": 2_970_000, "nnz": 5_940_000, "precision": "fp64", "tol": 1e-8,
             "coarse_size": 25}
-METRIC = "Fiedler solves/s (CMG setup + solve, 3D grid 1M vertices, FP64)"
+# The timed step is one whole CMG solve; inputs (71 MB of CSR) are smaller than
+# L2 (129 MB), so L2 is flushed between timed steps.
+METRIC = "Fiedler solves/s (CMG setup + solve, 3D grid 1M vertices)"
 UNIT = "solves/s"
 
 
@@ -182,32 +184,32 @@ def run_gpu(args):
     drp = torch.from_numpy(rp).cuda()
     dcol = torch.from_numpy(col).cuda()
     dw = torch.from_numpy(w).cuda()
-    u = torch.empty(n, dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     sid = stream.cuda_stream
-    opts = cmg.options(seed=1412, timing=1)
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")  # > L2 (129 MB)
-
-    def step():
-        h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
-        _, lam, st = h.fiedler(u_out=u, stream=sid)
-        h.close()
-        return lam, st
-
-    for _ in range(max(3, args.warmup)):
-        step()
-    torch.cuda.synchronize()
 
     def barrier():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
 
-    launches0 = cmg.kernel_launches()
-    step_ms, stats = [], []
-    barrier()
-    with ClockSampler(local) as clk:
-        for _ in range(args.steps):
+    def measure(precision, steps, warmup):
+        """Timed steps of setup + solve with device-resident inputs."""
+        opts = cmg.options(seed=1412, timing=1, precision=precision)
+        u = torch.empty(n, dtype=torch.float64, device="cuda")
+
+        def step():
+            h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
+            _, lam, st = h.fiedler(u_out=u, stream=sid)
+            h.close()
+            return lam, st
+
+        for _ in range(max(3, warmup)):
+            step()
+        barrier()
+        l0 = cmg.kernel_launches()
+        step_ms, stats = [], []
+        for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -218,25 +220,34 @@ def run_gpu(args):
             step_ms.append(e0.elapsed_time(e1))
             stats.append(st)
         barrier()
-    launches = cmg.kernel_launches() - launches0 - 0
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+        launches = cmg.kernel_launches() - l0
+        total = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total = float(t.item())
+        srt = sorted(step_ms)
+        return {"value": world * steps / (total / 1e3), "ms_per_step": total / steps,
+                "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                "stats": stats, "launches": launches, "u": u.cpu().numpy(), "lam": lam}
 
-    # ---- roofline of the dominant kernel: the power-iteration launches (k_power)
-    st0 = stats[-1]
-    ns, nnzs, sweeps = st0["n"], st0["nnz"], st0["sweeps"]
-    L = len(ns)
-    pi_bytes = 0
-    for j in range(L):
-        nc = ns[j + 1] if j + 1 < L else 0
-        pi_bytes += level_launch_bytes(ns[j], nnzs[j], sweeps[j], nc)
-    pi_ms = statistics.median(sum(s["level_ms"]) for s in stats)
-    lvl0_ms = statistics.median(s["level_ms"][0] for s in stats)
-    lvl0_bytes = level_launch_bytes(ns[0], nnzs[0], sweeps[0], ns[1] if L > 1 else 0)
+    with ClockSampler(local) as clk:
+        r32 = measure("fp32", args.steps, args.warmup)
+        r64 = measure("fp64", args.steps, args.warmup)
+    clocks = clk.summary()
+
+    # ---- roofline of the dominant kernel: the level-0 power-iteration launch
+    def roofline(r, fp32):
+        st0 = r["stats"][-1]
+        ns, nnzs, sweeps = st0["n"], st0["nnz"], st0["sweeps"]
+        L = len(ns)
+        ms0 = statistics.median(s["level_ms"][0] for s in r["stats"])
+        by0 = level_launch_bytes(ns[0], nnzs[0], sweeps[0], ns[1] if L > 1 else 0, fp32)
+        tot_b = sum(level_launch_bytes(ns[j], nnzs[j], sweeps[j], ns[j + 1] if j + 1 < L else 0, fp32)
+                    for j in range(L))
+        tot_ms = statistics.median(sum(s["level_ms"]) for s in r["stats"])
+        return ms0, by0, tot_b, tot_ms, st0
+
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -247,15 +258,23 @@ def run_gpu(args):
     peak_src = "measured" if hbm_peak else "fallback"
     if not hbm_peak:
         hbm_peak = 6800.0
-    achieved0 = lvl0_bytes / (lvl0_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": "k_power (level 0 launch)", "achieved": achieved0,
-                "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-                "frac": achieved0 / hbm_peak, "traffic": None,
-                "bytes_per_launch": lvl0_bytes, "launch_ms": lvl0_ms,
-                "all_levels": {"bytes": pi_bytes, "ms": pi_ms,
-                               "achieved": pi_bytes / (pi_ms * 1e-3) / 1e9}}
+    ms0, by0, tot_b, tot_ms, st32 = roofline(r32, True)
+    achieved0 = by0 / (ms0 * 1e-3) / 1e9
+    roof = {"bound": "hbm", "kernel": "k_power_tiled<float>, level-0 launch",
+            "achieved": achieved0, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+            "frac": achieved0 / hbm_peak, "traffic": None, "bytes_per_launch": by0,
+            "launch_ms": ms0, "sweeps_per_launch": st32["sweeps"][0],
+            "all_levels": {"bytes": tot_b, "ms": tot_ms, "achieved": tot_b / (tot_ms * 1e-3) / 1e9}}
+    ms0_64, by0_64, tot_b64, tot_ms64, st64 = roofline(r64, False)
 
-    # ---- end to end through the public API with host buffers
+    # accuracy of the FP32-sweep form against the plain FP64 form
+    u32, u64 = r32["u"], r64["u"]
+    cosang = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
+    acc = {"lambda2_rel_diff": abs(r32["lam"] - r64["lam"]) / abs(r64["lam"]),
+           "angle_rad": float(np.arccos(min(1.0, cosang))),
+           "note": "FP32-sweep result vs plain FP64 GPU result, tolerance-mode sweep counts differ"}
+
+    # ---- end to end through the public API with host buffers (FP32 form)
     e2e_ms = []
     hu = np.empty(n, dtype=np.float64)
     rp_h = np.ascontiguousarray(rp)
@@ -265,19 +284,19 @@ def run_gpu(args):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = cmg.Hierarchy(rp_h, col, w, seed=1412, stream=sid)
+        h = cmg.Hierarchy(rp_h, col, w, seed=1412, precision="fp32", stream=sid)
         h.fiedler(u_out=hu, stream=sid)
         h.close()
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = world * len(e2e_ms) / (sum(e2e_ms) / 1e3)
+    e2e_tot = sum(e2e_ms)
     if world > 1:
-        t = torch.tensor([sum(e2e_ms)], dtype=torch.float64, device="cuda")
+        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_val = world * len(e2e_ms) / (float(t.item()) / 1e3)
+        e2e_tot = float(t.item())
+    e2e_val = world * len(e2e_ms) / (e2e_tot / 1e3)
 
-    line = None
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -289,26 +308,34 @@ def run_gpu(args):
                 reps += 1
             dt = time.perf_counter() - t0
             cpu = {"value": reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{reps} full CMG solves (setup+solve) of the same 1M-vertex grid, "
+                   "sample": f"{reps} full CMG solves (setup+solve, FP64) of the same 1M-vertex grid, "
                              f"single-threaded C oracle on {cpu_info()}"}
-        ms_sorted = sorted(step_ms)
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 sweeps, f64 final sweep / Rayleigh quotient, float-float reductions",
             "data": "synthetic",
-            "config": dict(WORKLOAD, l2="256 MB buffer written between timed steps (flush)",
+            "config": dict(WORKLOAD, precision="fp32-sweep",
+                           l2="256 MB buffer written between timed steps (flush)",
                            parallelism=f"replicas{world}"),
-            "latency_ms": {"p50": ms_sorted[len(ms_sorted) // 2],
-                           "p99": ms_sorted[min(len(ms_sorted) - 1, int(0.99 * len(ms_sorted)))]},
-            "levels": {"n": ns, "nnz": nnzs, "sweeps": sweeps,
-                       "level_ms": [round(x, 4) for x in st0["level_ms"]]},
-            "lambda2": st0["lambda2"], "residual": st0["residual"],
-            "roofline": roofline, "cpu_baseline": cpu,
+            "latency_ms": {"p50": r32["p50_ms"], "p99": r32["p99_ms"]},
+            "levels": {"n": st32["n"], "nnz": st32["nnz"], "sweeps": st32["sweeps"],
+                       "level_ms": [round(x, 4) for x in st32["level_ms"]]},
+            "lambda2": st32["lambda2"], "residual": st32["residual"],
+            "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
+                     "latency_ms": {"p50": r64["p50_ms"], "p99": r64["p99_ms"]},
+                     "sweeps": st64["sweeps"], "level_ms": [round(x, 4) for x in st64["level_ms"]],
+                     "lambda2": st64["lambda2"], "residual": st64["residual"],
+                     "level0_launch": {"ms": ms0_64, "bytes": by0_64,
+                                       "achieved_gbs": by0_64 / (ms0_64 * 1e-3) / 1e9},
+                     "gpu_launches": r64["launches"]},
+            "fp32_vs_fp64": acc,
+            "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n},
-            "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "gpu_launches": r32["launches"],
+            "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -226,7 +226,7 @@ cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int3
  * errors as cmg_power_sweeps, except:
  *   - n <= CMG_NOALLOC_MAX_N and nnz <= CMG_NOALLOC_MAX_NNZ; larger graphs
  *     are rejected with CMG_ERR_TOO_LARGE before any device work;
- *   - its scratch is one fixed array of about 4.3 MB in device memory that
+ *   - its scratch is one fixed array of about 8.4 MB in device memory that
  *     every GPU which loads this library holds until the process exits;
  *   - the first call on a device looks up that array's device address
  *     (cudaGetSymbolAddress) with the device current; make that first call

@@ -97,7 +97,8 @@ struct cmg_hierarchy_s {
     cmg_options_t opts;
     std::vector<LevelData> lv;
     // solve workspace
-    std::vector<void *> bufs;  // 2 per level
+    std::vector<void *> bufs;  // 3 per level (iterate ring)
+    std::vector<double *> gd;  // FP64 form: g - d_i per level
     PiResult *res = nullptr;   // one per level
     GridSync *gs = nullptr;
     double *out2 = nullptr;
@@ -122,6 +123,7 @@ static void free_hierarchy(cmg_hierarchy_s *h) {
     cudaSetDevice(h->device);
     for (auto &L : h->lv) free_level(L, h->stream);
     for (void *p : h->bufs) dev_free(p, h->stream);
+    for (double *p : h->gd) dev_free(p, h->stream);
     dev_free(h->res, h->stream);
     dev_free(h->gs, h->stream);
     dev_free(h->out2, h->stream);
@@ -267,11 +269,14 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     // ---- solve workspace: a buffer pair per level, results, barrier state
     const size_t esz = (o.precision == CMG_PRECISION_FP32_SWEEP) ? sizeof(float) : sizeof(double);
     for (auto &L : h->lv) {
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < 3; k++) {
             void *p = nullptr;
             CMG_TRY(dev_alloc(&p, esz * (size_t)L.n, s));
             h->bufs.push_back(p);
         }
+        double *gdp = nullptr;
+        if (o.precision == CMG_PRECISION_FP64) CMG_TRY(dev_alloc_n(&gdp, (size_t)L.n, s));
+        h->gd.push_back(gdp);
     }
     CMG_TRY(dev_alloc_n(&h->res, h->lv.size(), s));
     CMG_TRY(dev_alloc_n(&h->gs, 1, s));
@@ -283,7 +288,8 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         bytes += sizeof(int) * ((size_t)L.n + 1) + (sizeof(int) + sizeof(double)) * (size_t)L.nnz;
         if (L.w32) bytes += sizeof(float) * (size_t)L.nnz;
         if (L.agg) bytes += sizeof(int) * (size_t)L.n;
-        bytes += 2 * esz * (size_t)L.n;
+        bytes += 3 * esz * (size_t)L.n;
+        if (o.precision == CMG_PRECISION_FP64) bytes += sizeof(double) * (size_t)L.n;
     }
     bytes += sizeof(double) * (size_t)n;
     h->bytes = bytes;
@@ -409,13 +415,12 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
             r.k_fixed = o.replay_sweeps[j];
         }
         if (j < J) {
-            r.coarse_buf = h->bufs[2 * (j + 1)];
-            r.coarse_buf1 = h->bufs[2 * (j + 1) + 1];
+            for (int k = 0; k < 3; k++) r.coarse_bufs[k] = h->bufs[3 * (j + 1) + k];
             r.coarse_res = h->res + (j + 1);
             r.coarse_agg = h->lv[j].agg;
         }
-        r.bufs[0] = h->bufs[2 * j];
-        r.bufs[1] = h->bufs[2 * j + 1];
+        for (int k = 0; k < 3; k++) r.bufs[k] = h->bufs[3 * j + k];
+        r.gd = h->gd[j];
         r.res = h->res + j;
         if (timing) cudaEventRecord(ev[2 * j], s);
         st = power_iteration(r, h->gs, s);
@@ -424,7 +429,7 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
     double *u_dev = (u_out && u_mem == CMG_MEM_DEVICE) ? u_out : h->u_dev;
     if (timing && st == CMG_OK) cudaEventRecord(ev[2 * (J + 1)], s);
     if (st == CMG_OK)
-        st = finalize(views[0], fp32, h->bufs[0], h->bufs[1], h->res, u_dev, 1, 0, h->out2, h->gs, s);
+        st = finalize(views[0], fp32, &h->bufs[0], h->res, u_dev, 1, 0, h->out2, h->gs, s);
     if (timing && st == CMG_OK) cudaEventRecord(ev[2 * (J + 1) + 1], s);
     std::vector<PiResult> hr(J + 1);
     double out2[2] = {0.0, 0.0};
@@ -598,11 +603,11 @@ cmg_status_t cmg_power_sweeps(int32_t n, const int32_t *row_ptr, const int32_t *
     lv.col = col;
     lv.w = w;
     lv.g = g;
-    double *b0, *b1, *out2;
+    double *b[3], *gd, *out2;
     PiResult *res;
     GridSync *gs;
-    CMG_TRY(scr.get(&b0, n));
-    CMG_TRY(scr.get(&b1, n));
+    for (int q = 0; q < 3; q++) CMG_TRY(scr.get(&b[q], n));
+    CMG_TRY(scr.get(&gd, n));
     CMG_TRY(scr.get(&res, 1));
     CMG_TRY(scr.get(&gs, 1));
     CMG_TRY(scr.get(&out2, 2));
@@ -612,11 +617,12 @@ cmg_status_t cmg_power_sweeps(int32_t n, const int32_t *row_ptr, const int32_t *
     r.k_fixed = k;
     r.max_sweeps = k;
     r.x_init = x_in;
-    r.bufs[0] = b0;
-    r.bufs[1] = b1;
+    for (int q = 0; q < 3; q++) r.bufs[q] = b[q];
+    r.gd = gd;
     r.res = res;
+    void *bv[3] = {b[0], b[1], b[2]};
     CMG_TRY(power_iteration(r, gs, s));
-    CMG_TRY(finalize(lv, 0, b0, b1, res, u_out, 0, 0, out2, gs, s));
+    CMG_TRY(finalize(lv, 0, bv, res, u_out, 0, 0, out2, gs, s));
     PiResult hr;
     GridSync hgs;
     CMG_CUDA(cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, s));
@@ -645,7 +651,7 @@ cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int3
     GridSync *gs;
     CMG_TRY(scr.get(&out2, 2));
     CMG_TRY(scr.get(&gs, 1));
-    CMG_TRY(finalize(lv, 0, nullptr, nullptr, nullptr, const_cast<double *>(u), 0, 1, out2, gs, s));
+    CMG_TRY(finalize(lv, 0, nullptr, nullptr, const_cast<double *>(u), 0, 1, out2, gs, s));
     double h2[2];
     GridSync hgs;
     CMG_CUDA(cudaMemcpyAsync(h2, out2, sizeof(h2), cudaMemcpyDeviceToHost, s));

@@ -93,43 +93,71 @@ __device__ __forceinline__ unsigned long long global_ns() {
 // A barrier wait gives up after this long and sets GridSync::err.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
 
+__device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int ld_relaxed_gpu(const unsigned int *p) {
+    unsigned int v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ unsigned int atom_add_acq_rel_gpu(unsigned int *p, unsigned int v) {
+    unsigned int old;
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+__device__ __forceinline__ void st_relaxed_gpu(unsigned int *p, unsigned int v) {
+    asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void red_add_release_gpu(unsigned int *p, unsigned int v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" :: "l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier for a cooperative launch (all CTAs co-resident).  Every
-// thread of every CTA must call it.  Returns false (in every thread of the
-// CTA) when the barrier or an earlier one timed out; callers then return.
+// thread of every CTA must call it.  Arrival is an acq_rel atomic on a
+// counter (releasing the CTA's writes, ordered before it by __syncthreads);
+// the last arriver resets the counter and releases a generation number that
+// the others poll with acquire loads.  A wait gives up after
+// kBarrierTimeoutNs and sets GridSync::err.  Returns false (in every thread
+// of the CTA) when this or an earlier barrier timed out; callers then return.
 __device__ __forceinline__ bool grid_sync(GridSync *gs) {
     __shared__ int s_ok;
     __syncthreads();
-    if (gridDim.x == 1) {
-        return true;
-    }
+    if (gridDim.x == 1) return true;
     if (threadIdx.x == 0) {
-        volatile unsigned int *vgen = &gs->gen;
-        volatile unsigned int *verr = &gs->err;
-        unsigned int g0 = *vgen;
-        __threadfence();
-        unsigned int arrived = atomicAdd(&gs->count, 1u);
+        const unsigned int g0 = ld_relaxed_gpu(&gs->gen);
+        const unsigned int arrived = atom_add_acq_rel_gpu(&gs->count, 1u);
         int ok = 1;
         if (arrived == gridDim.x - 1) {
-            atomicExch(&gs->count, 0u);
-            __threadfence();
-            atomicAdd(&gs->gen, 1u);
+            st_relaxed_gpu(&gs->count, 0u);
+            red_add_release_gpu(&gs->gen, 1u);
         } else {
-            unsigned long long t0 = global_ns();
-            while (*vgen == g0) {
-                if (*verr) {
-                    ok = 0;
-                    break;
+            unsigned long long t0 = 0;
+            for (unsigned int spin = 0;; spin++) {
+                if (ld_acquire_gpu(&gs->gen) != g0) break;
+                if ((spin & 1023u) == 1023u) {
+                    const unsigned long long t = global_ns();
+                    if (t0 == 0) {
+                        t0 = t;
+                    } else if (t - t0 > kBarrierTimeoutNs) {
+                        atomicExch(&gs->err, 1u);
+                        ok = 0;
+                        break;
+                    }
+                    if (ld_relaxed_gpu(&gs->err)) {
+                        ok = 0;
+                        break;
+                    }
                 }
-                if (global_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicExch(&gs->err, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(32);
             }
         }
-        __threadfence();
-        if (*verr) ok = 0;
+        if (ld_relaxed_gpu(&gs->err)) ok = 0;
         s_ok = ok;
     }
     __syncthreads();

@@ -54,10 +54,12 @@ struct PiResult {
     double cos;      // cosine between the last two iterates
     double mu_prev;  // scalars of the previous iterate (used by the FP64 final sweep)
     double inv_s_prev;
-    int buf;         // index (0/1) of the buffer that holds the raw result
+    int buf;         // index (0..2) of the buffer that holds the raw result
+    int buf_prev;    // index of the buffer that holds the previous iterate
     int sweeps;
     int capped;
-    int zero;        // R10: the last sweep produced the zero vector
+    int zero;        // the last sweep annihilated the iterate (B_g v = 0)
+    int pad;
 };
 
 struct PiLevel {
@@ -79,9 +81,10 @@ cmg_status_t build_tiles(int n, long long nnz, const int *rp, int *tile_row, cud
 
 // Power iteration (Alg. 3) on one level.  Start vector: x_init if given;
 // else, if coarse_res is given, the prolongation (I_j^{j+1})^T of the coarse
-// result held in coarse_buf / coarse_buf1 (whichever coarse_res->buf names);
-// else the Gaussian start of Alg. 1 Step 2 keyed by `seed`.
-// bufs: two vectors of n elements (double, or float when fp32).
+// result held in coarse_bufs[coarse_res->buf]; else the Gaussian start of
+// Alg. 1 Step 2 keyed by `seed`.
+// bufs: three vectors of n elements (double, or float when fp32) and, for
+// FP64, gd: n doubles of scratch for g - d_i.
 // mode 0: stop on the cosine rule or after max_sweeps; mode 1: exactly k_fixed sweeps.
 struct PiRun {
     const PiLevel *lv;
@@ -91,12 +94,12 @@ struct PiRun {
     int max_sweeps;
     double tol;
     uint64_t seed;
-    const void *coarse_buf;
-    const void *coarse_buf1;
+    const void *coarse_bufs[3];
     const PiResult *coarse_res;
     const int *coarse_agg;           // agg of this level onto the coarse level
     const double *x_init;
-    void *bufs[2];
+    void *bufs[3];
+    double *gd;
     PiResult *res;
 };
 // Caller-provided scratch for power_iteration / finalize (nullptr: the
@@ -119,8 +122,8 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s,
 //   - if `sign`: scale u so that its largest-|u_i| entry (lowest index on
 //     ties) is positive;
 //   - out2[0] = u^T L u / u^T u, out2[1] = ||(L - out2[0] I) u|| / ||u||.
-cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void *buf1,
-                      const PiResult *res, double *u, int sign, int fresh, double *out2,
-                      GridSync *gs, cudaStream_t s, const PiWorkspace *ws = nullptr);
+cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const PiResult *res,
+                      double *u, int sign, int fresh, double *out2, GridSync *gs, cudaStream_t s,
+                      const PiWorkspace *ws = nullptr);
 
 }  // namespace cmg

@@ -1,7 +1,7 @@
 // noalloc.cu -- cmg_power_sweeps_noalloc: the fixed-count power sweeps of
 // cmg_power_sweeps without any device allocation.
 //
-// Its scratch (two iterate vectors, row tiles, partial sums, the result
+// Its scratch (three iterate vectors, g - d_i, row tiles, partial sums, the result
 // record, barrier state and the shift) lives in one file-scope __device__
 // array.  Host code must not use the array's name as a device address: on
 // first use on a device, with that device current, the address is looked up
@@ -16,14 +16,15 @@ namespace {
 
 constexpr int kMaxN = CMG_NOALLOC_MAX_N;
 constexpr long long kMaxNnz = CMG_NOALLOC_MAX_NNZ;
-constexpr int kTileCap = 2048;             // >= (kMaxNnz + 4 kMaxN) / 4096 + 1
+constexpr int kTileCap = 2048;             // >= (kMaxNnz + 4 kMaxN) / 3840 + 2
 constexpr int kPartCap = 2 * 1024 * 5;     // sweep partial sums, up to 1024 CTAs
 constexpr int kFinCap = 12 * 1024;         // final-pass partial sums, up to 1024 CTAs
 
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-constexpr size_t kOffB0 = 0;
-constexpr size_t kOffB1 = kOffB0 + align256(sizeof(double) * kMaxN);
-constexpr size_t kOffTiles = kOffB1 + align256(sizeof(double) * kMaxN);
+constexpr size_t kVec = align256(sizeof(double) * kMaxN);
+constexpr size_t kOffB0 = 0;                 // iterate ring: 3 vectors
+constexpr size_t kOffGd = kOffB0 + 3 * kVec; // g - d_i
+constexpr size_t kOffTiles = kOffGd + kVec;
 constexpr size_t kOffPart = kOffTiles + align256(sizeof(int) * kTileCap);
 constexpr size_t kOffFin = kOffPart + align256(sizeof(double) * kPartCap);
 constexpr size_t kOffRes = kOffFin + align256(sizeof(double) * kFinCap);
@@ -73,8 +74,9 @@ extern "C" cmg_status_t cmg_power_sweeps_noalloc(int32_t n, const int32_t *row_p
     const long long nnz = nnz_i;
     if (nnz < 0) return CMG_ERR_INVALID_ARG;
     if (nnz > kMaxNnz) return CMG_ERR_TOO_LARGE;
-    double *b0 = reinterpret_cast<double *>(base + kOffB0);
-    double *b1 = reinterpret_cast<double *>(base + kOffB1);
+    void *ring[3];
+    for (int q = 0; q < 3; q++) ring[q] = base + kOffB0 + q * kVec;
+    double *gdv = reinterpret_cast<double *>(base + kOffGd);
     PiResult *res = reinterpret_cast<PiResult *>(base + kOffRes);
     GridSync *gs = reinterpret_cast<GridSync *>(base + kOffSync);
     double *out2 = reinterpret_cast<double *>(base + kOffOut);
@@ -104,11 +106,11 @@ extern "C" cmg_status_t cmg_power_sweeps_noalloc(int32_t n, const int32_t *row_p
     r.k_fixed = k;
     r.max_sweeps = k;
     r.x_init = x_in;
-    r.bufs[0] = b0;
-    r.bufs[1] = b1;
+    for (int q = 0; q < 3; q++) r.bufs[q] = ring[q];
+    r.gd = gdv;
     r.res = res;
     CMG_TRY(power_iteration(r, gs, s, &ws));
-    CMG_TRY(finalize(lv, 0, b0, b1, res, u_out, 0, 0, out2, gs, s, &ws));
+    CMG_TRY(finalize(lv, 0, ring, res, u_out, 0, 0, out2, gs, s, &ws));
     PiResult hr;
     GridSync hgs;
     CMG_CUDA(cudaMemcpyAsync(&hr, res, sizeof(hr), cudaMemcpyDeviceToHost, s));

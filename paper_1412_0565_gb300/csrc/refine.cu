@@ -1,45 +1,65 @@
 // refine.cu -- power iteration (Alg. 3 of arXiv 1412.0565), the final vector,
 // its sign, and the Rayleigh quotient / residual of Sec. 4.
 //
-// A sweep computes u <- B_g v = g v - L v, projects u against 1 and
-// normalises it (Alg. 3; the projection is repeated every sweep, which equals
-// Alg. 3 in exact arithmetic and keeps rounding from growing along 1, the
-// dominant eigenvector of B_g).  The normalised iterate is never stored: a
-// buffer holds the raw vector y and scalars (mu, 1/s) with u = (y - mu) / s,
-// and the next sweep applies B_g to u on the fly,
-//     (B_g u)_i = [ g (y_i - mu) - sum_j w_ij (y_i - y_j) ] / s
-// (edge-difference form of L; mu cancels inside the differences).  The same
-// pass accumulates sum y, sum y^2, sum y u_prev, sum u_prev, sum u_prev^2 in
-// FP64, from which the next (mu, s) and the stopping cosine cos(u^k, u^{k-1})
-// follow.  Every combination of partial sums runs in a fixed order, so results
-// are bitwise reproducible and all CTAs take the same stop decision.
+// Alg. 3 iterates u <- B_g v / ||B_g v|| with B_g = g I - L, after one
+// Gram-Schmidt step against 1, and stops when cos(u^k, u^{k-1}) >= 1 - tol.
+// Here the iterate is kept unnormalised, y_s = sigma_{s-1} (B_g y_{s-1} -
+// g m_{s-1} 1), with sigma = 2^e / g (an exact power-of-two rescale keeps
+// ||y|| near 1) and m an estimate of the mean of y_{s-1}, so that u_s is
+// (y_s - mean(y_s)) / ||y_s - mean(y_s)||: the same vector as Alg. 3's in exact
+// arithmetic, since 1 is an eigenvector of B_g.  Each sweep accumulates
+//     A_s = sum y_s,  B_s = sum y_s^2,  C_s = sum y_s y_{s-1}
+// from which mean, norm and the stopping cosine follow:
+//     mu_s = A_s / n,  ss_s = B_s - n mu_s^2,
+//     cos_s = (C_s - n mu_s mu_{s-1}) / sqrt(ss_s ss_{s-1}).
+// Those sums are reduced by a dedicated control warp while the other warps
+// compute the next sweep, so no reduction is on the critical path: the stop
+// decision for sweep s is taken during sweep s+1 (whose result is then
+// discarded; the iterates live in a ring of three buffers), and the mean
+// estimate for sweep s+2 is m_{s+1} = 2^{e_s} (mu_s - m_s), the propagated
+// 1-component of y_s, which keeps that component at rounding level.
+//
+// Sums and scalars are float-float (ffloat.cuh) on the FP32 pipe; FP64 is
+// used where the FP64 form computes its sweeps, and for the final scalars.
 //
 // Two kernels:
-//   k_power_tiled  large levels: a cooperative persistent kernel, one grid
-//                  barrier per sweep.  The rows are cut into tiles of at most
-//                  kTileRows rows and about kChunk entries; a tile's column
-//                  indices and weights are streamed with coalesced loads, all
-//                  its x gathers are in flight at once, and the products are
-//                  summed per row, left to right, in shared memory.
-//   k_power_small  small levels: one CTA holds the level's CSR and both
-//                  vectors in shared memory; a sweep costs two __syncthreads.
+//   k_power_tiled  large levels: cooperative persistent kernel, one grid
+//                  barrier per sweep.  Rows are cut into tiles (at most
+//                  kTileRows rows, about kChunk entries); a tile's column
+//                  indices and weights stream in with coalesced loads, all
+//                  its x gathers are issued at once, and per-row sums run left
+//                  to right in shared memory.
+//   k_power_small  small levels: one CTA holds the CSR and the iterate ring in
+//                  shared memory; one __syncthreads per sweep.
 #include <algorithm>
 #include <math.h>
 
+#include "ffloat.cuh"
 #include "internal.h"
 
 namespace cmg {
 
 // Loads of data written by other CTAs of the same launch go through L2.
 #define LDX(p) __ldcg(p)
+// Gathers of the iterate: ordinary (L1-cached) loads.  The iterate read in a
+// sweep was written before the preceding grid barrier, whose acquire by the
+// CTA's thread 0 (followed by __syncthreads) orders these loads after the
+// writes; the parity tests check this bit for bit against L2-only loads.
+#ifdef CMG_X_LDCG
+#define LDXG(p) __ldcg(p)
+#else
+#define LDXG(p) (*(p))
+#endif
 
-constexpr int kNumPartials = 5;
-constexpr int kTileThreads = 512;
-constexpr int kTileRows = 1024;      // rows per tile (cost units: 4 per row)
-constexpr int kChunk = 4096;         // entries per chunk of a tile
-constexpr int kTileCost = 4096;      // cost of a tile: entries + 4 * rows
-constexpr int kSmallThreads = 1024;
+constexpr int kTileThreads = 512;                 // warp 0: control, 15 row warps
+constexpr int kRowThreads = kTileThreads - 32;
+constexpr int kU = 8;                             // entries per row thread per chunk
+constexpr int kChunk = kRowThreads * kU;          // 3840 entries
+constexpr int kTileRows = 960;
+constexpr int kTileCost = 3840;                   // entries + 4 * rows per tile
+constexpr int kSmallMaxThreads = 1024;
 constexpr int kFinThreads = 256;
+constexpr float kZeroTol2f = 2.0194839e-28f;  // (64 eps_64)^2
 
 struct PiArgs {
     int n;
@@ -55,16 +75,15 @@ struct PiArgs {
     int max_sweeps;
     double tol;
     uint64_t seed;
-    int start;             // 0 Gaussian, 1 prolongation, 2 explicit
-    const void *cbuf0;     // coarse level buffers (start = 1)
-    const void *cbuf1;
+    int start;              // 0 Gaussian, 1 prolongation, 2 explicit
+    const void *cbuf[3];    // coarse ring (start = 1)
     const PiResult *cres;
     const int *agg;
-    const double *x_init;  // start = 2
-    void *buf0;
-    void *buf1;
+    const double *x_init;   // start = 2
+    void *buf[3];           // iterate ring
+    double *gd;             // FP64 form: g - d_i
     PiResult *res;
-    double *partials;      // [2][gridDim.x][kNumPartials]
+    ff *partials;           // [2][gridDim.x][3] (tiled kernel)
 };
 
 __device__ __forceinline__ uint64_t sm64(uint64_t x) {
@@ -94,52 +113,800 @@ __device__ __forceinline__ double start_value(const PiArgs &a, int i, const T *c
     return a.x_init[i];
 }
 
-// Iteration state shared by both kernels.
-struct SweepState {
-    double mu, inv_s, mu_prev, inv_prev, cosv;
-    int cur, k, zero;
+// ------------------------------------------------------------------ partial sums
+struct Part {
+    ff A, B, C;
 };
 
-// Scalars after a sweep from the sums S; returns true when the iteration stops.
-__device__ __forceinline__ bool after_sweep(const PiArgs &a, const double *S, int n, SweepState &st) {
-    st.k++;
-    const double muy = S[0] / (double)n;
-    double ss = S[1] - (double)n * muy * muy;
-    if (ss < 0.0) ss = 0.0;
-    const double den = sqrt(ss * S[4]);
-    st.cosv = den > 0.0 ? (S[2] - muy * S[3]) / den : 1.0;
-    // B_g annihilated the unit iterate to rounding level: it is an
-    // eigenvector of L with eigenvalue g (e.g. n = 2); keep it and stop
-    if (sqrt(ss) <= 64.0 * 2.220446049250313e-16 * a.g) {
-        st.zero = 1;
-        return true;
-    }
-    st.mu_prev = st.mu;
-    st.inv_prev = st.inv_s;
-    st.mu = muy;
-    st.inv_s = 1.0 / sqrt(ss);
-    st.cur ^= 1;
-    if (a.mode == 1) return st.k >= a.k_fixed;
-    if (!(st.cosv < 1.0 - a.tol)) return true;
-    return st.k >= a.max_sweeps;
+__device__ __forceinline__ Part part_zero() {
+    Part p;
+    p.A = p.B = p.C = ff_zero();
+    return p;
 }
 
-__device__ __forceinline__ void write_result(const PiArgs &a, const SweepState &st, bool run) {
+__device__ __forceinline__ Part part_add(Part x, Part y) {
+    Part r;
+    r.A = ff_add(x.A, y.A);
+    r.B = ff_add(x.B, y.B);
+    r.C = ff_add(x.C, y.C);
+    return r;
+}
+
+__device__ __forceinline__ Part warp_sum_part(Part p) {
+    p.A = warp_sum_ff(p.A);
+    p.B = warp_sum_ff(p.B);
+    p.C = warp_sum_ff(p.C);
+    return p;
+}
+
+// Per-thread accumulation of (sum y, sum y^2, sum y x) for one sweep.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    ff A, B, C;
+    __device__ __forceinline__ void reset() { A = B = C = ff_zero(); }
+    __device__ __forceinline__ void add(float y, float x) {
+        A = ff_add_f(A, y);
+        B = ff_add(B, two_prod(y, y));
+        C = ff_add(C, two_prod(y, x));
+    }
+    __device__ __forceinline__ Part get() const {
+        Part p;
+        p.A = A;
+        p.B = B;
+        p.C = C;
+        return p;
+    }
+};
+
+template <>
+struct Acc<double> {
+    double A, B, C;
+    __device__ __forceinline__ void reset() { A = B = C = 0.0; }
+    __device__ __forceinline__ void add(double y, double x) {
+        A += y;
+        B = fma(y, y, B);
+        C = fma(y, x, C);
+    }
+    __device__ __forceinline__ Part get() const {
+        Part p;
+        p.A = ff_from_double(A);
+        p.B = ff_from_double(B);
+        p.C = ff_from_double(C);
+        return p;
+    }
+};
+
+// ------------------------------------------------------------------ control
+// Sweep parameters and decisions, double-buffered by sweep parity in shared
+// memory.  Slot for sweep t holds what the rows of sweep t need (m_{t-1},
+// e_{t-1}) and the stop decision taken for sweep t-2.
+struct Slot {
+    ff m;           // mean estimate to subtract
+    int e;          // power-of-two rescale exponent
+    int stop;       // decision for sweep t-2: 0 continue, 1 stop
+    int zero;       // that sweep annihilated the iterate
+    int pad;
+};
+
+__device__ __forceinline__ Slot slot_make(ff m, int e) {
+    Slot sl;
+    sl.m = m;
+    sl.e = e;
+    sl.stop = 0;
+    sl.zero = 0;
+    sl.pad = 0;
+    return sl;
+}
+
+// Scalars of the reduced sweeps, kept by the control warp (all lanes hold
+// the same values).
+struct Ctl {
+    ff mu_prev, ss_prev;   // mean and squared norm of y_{s-1}
+    ff m_cur;              // m_s: used by sweep s+1
+    ff inv_n, omt2;        // 1/n and (1 - tol)^2
+    int e_cur, e_prev;     // e_s, e_{s-1}
+    // result of the decision (valid once `stopped`)
+    int stopped, zero, res_sweep, capped;
+    double mu_res, ss_res, mu_res_prev, ss_res_prev, cos_res;
+};
+
+__device__ __forceinline__ double to_d(ff a) { return ff_to_double(a); }
+
+// One control step for sweep s (s >= 1) with its reduced sums P.  Decides,
+// and fills the slot for sweep s+2 (m_{s+1}, e_{s+1}).  `count_exit`: the
+// loop ends after sweep s regardless (fixed count or sweep cap reached).
+__device__ __forceinline__ void ctrl_step(const PiArgs &a, int s, const Part &P, Ctl &c,
+                                          Slot *next, bool count_exit) {
+    const float nf = (float)a.n;
+    const ff mu = ff_mul(P.A, c.inv_n);
+    const ff ss = ff_sub(P.B, ff_mul_f(ff_mul(mu, mu), nf));
+    const ff cs = ff_sub(P.C, ff_mul_f(ff_mul(mu, c.mu_prev), nf));
+    // annihilated: ||proj y_s|| <= 64 eps 2^{e_{s-1}} ||proj y_{s-1}||
+    const bool zero = ss.hi <= kZeroTol2f * ldexpf(c.ss_prev.hi, 2 * c.e_prev);
+    // cos_s >= 1 - tol  <=>  cs > 0 and cs^2 >= (1 - tol)^2 ss_s ss_{s-1}
+    const bool conv = cs.hi > 0.f && !ff_lt(ff_mul(cs, cs), ff_mul(ff_mul(ss, c.ss_prev), c.omt2));
+    bool stop = zero;
+    if (a.mode == 0) stop = stop || conv || count_exit;
+    else stop = stop || count_exit;
+    if (stop && !c.stopped) {
+        c.stopped = 1;
+        c.zero = zero;
+        c.res_sweep = s;
+        if (zero) {
+            c.mu_res = to_d(c.mu_prev);
+            c.ss_res = to_d(c.ss_prev);
+            c.cos_res = 1.0;
+        } else {
+            c.mu_res = to_d(mu);
+            c.ss_res = to_d(ss);
+            c.mu_res_prev = to_d(c.mu_prev);
+            c.ss_res_prev = to_d(c.ss_prev);
+            const double den = sqrt(c.ss_res * c.ss_res_prev);
+            c.cos_res = den > 0.0 ? to_d(cs) / den : 1.0;
+        }
+        c.capped = (a.mode == 0 && !zero && !conv) ? 1 : 0;
+    }
+    // parameters of sweep s+2 (exact power-of-two scaling of mu_s - m_s)
+    const ff dm = ff_sub(mu, c.m_cur);
+    const ff m_next = ff_make(ldexpf(dm.hi, c.e_cur), ldexpf(dm.lo, c.e_cur));
+    int e_next = 0;
+    {
+        // predicted log2 ||y_{s+1}|| <= log2 ||y_s|| + e_s; lift it back to ~1
+        const float l2 = 0.5f * log2f(fmaxf(ss.hi, 1e-37f)) + (float)c.e_cur;
+        if (l2 < -24.f) e_next = (int)(-l2);
+    }
+    if (next) {
+        *next = slot_make(m_next, e_next);
+        next->stop = stop ? 1 : 0;
+        next->zero = zero ? 1 : 0;
+    }
+    c.mu_prev = mu;
+    c.ss_prev = ss;
+    c.m_cur = m_next;
+    c.e_prev = c.e_cur;
+    c.e_cur = e_next;
+}
+
+__device__ __forceinline__ void ctl_init(Ctl &c, const PiArgs &a, double mu0, double ss0, int e0) {
+    c.mu_prev = ff_from_double(mu0);
+    c.ss_prev = ff_from_double(ss0);
+    c.m_cur = ff_zero();   // m_1: the start was projected exactly
+    c.inv_n = ff_from_double(1.0 / (double)a.n);
+    const double omt = 1.0 - a.tol;
+    c.omt2 = ff_from_double(omt * omt);
+    c.e_cur = 0;
+    c.e_prev = e0;
+    c.stopped = 0;
+    c.zero = 0;
+    c.res_sweep = 0;
+    c.capped = 0;
+    c.mu_res = mu0;
+    c.ss_res = ss0;
+    c.mu_res_prev = mu0;
+    c.ss_res_prev = ss0;
+    c.cos_res = 0.0;
+}
+
+__device__ __forceinline__ int start_exponent(double ss0) {
+    // 2^e0 ~ 1 / ||proj y_0||
+    if (!(ss0 > 0.0)) return 0;
+    return -(int)floor(0.5 * log2(ss0) + 0.5);
+}
+
+__device__ __forceinline__ void write_result(const PiArgs &a, const Ctl &c, int buf, int buf_prev) {
     PiResult r;
-    r.mu = st.mu;
-    r.inv_s = st.inv_s;
-    r.cos = st.cosv;
-    r.mu_prev = st.mu_prev;
-    r.inv_s_prev = st.inv_prev;
-    r.buf = st.cur;
-    r.sweeps = st.k;
-    r.capped = (a.mode == 0 && run && !st.zero && st.cosv < 1.0 - a.tol) ? 1 : 0;
-    r.zero = st.zero;
+    r.mu = c.mu_res;
+    r.inv_s = c.ss_res > 0.0 ? 1.0 / sqrt(c.ss_res) : 0.0;
+    r.cos = c.cos_res;
+    r.mu_prev = c.mu_res_prev;
+    r.inv_s_prev = c.ss_res_prev > 0.0 ? 1.0 / sqrt(c.ss_res_prev) : 0.0;
+    r.buf = buf;
+    r.buf_prev = buf_prev;
+    r.sweeps = c.res_sweep;
+    r.capped = c.capped;
+    r.zero = c.zero;
+    r.pad = 0;
     *a.res = r;
 }
 
+template <typename T>
+__device__ __forceinline__ const T *wsel(const PiArgs &a);
+template <>
+__device__ __forceinline__ const double *wsel<double>(const PiArgs &a) { return a.w; }
+template <>
+__device__ __forceinline__ const float *wsel<float>(const PiArgs &a) { return a.w32; }
+
+// x * 2^e for a normal float x and a small e (exponent arithmetic, exact).
+__device__ __forceinline__ float scale2f(float x, int e) { return __int_as_float(__float_as_int(x) + (e << 23)); }
+
+template <typename P>
+__device__ __forceinline__ P pick3(P p0, P p1, P p2, int k) {
+    return k == 0 ? p0 : (k == 1 ? p1 : p2);
+}
+
+__device__ __forceinline__ void bar_rows(int nthreads) {
+    asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// ================================================================== tiled kernel
+template <typename T>
+struct TileSmem;
+// FP32: products; FP64: weights and gathered x (the row sum is an FMA chain)
+template <>
+struct TileSmem<float> {
+    float prod[kChunk];
+};
+template <>
+struct TileSmem<double> {
+    double wv[kChunk];
+    double xj[kChunk];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridSync *gs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TileSmem<T> &ts = *reinterpret_cast<TileSmem<T> *>(smem_raw);
+    T *s_x = reinterpret_cast<T *>(smem_raw + sizeof(TileSmem<T>));     // kTileRows
+    T *s_acc = s_x + kTileRows;                                         // kTileRows
+    int *s_rp = reinterpret_cast<int *>(s_acc + kTileRows);             // kTileRows + 1
+    unsigned short *s_row = reinterpret_cast<unsigned short *>(s_rp + kTileRows + 4);  // kChunk
+    __shared__ Part s_pw[kTileThreads / 32];
+    __shared__ Slot s_slot[2];
+
+    const int n = a.n;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tb = (int)((long long)a.ntiles * blockIdx.x / gridDim.x);
+    const int te = (int)((long long)a.ntiles * (blockIdx.x + 1) / gridDim.x);
+    const int r0 = a.tile_row[tb], r1 = a.tile_row[te];
+    T *const ring0 = (T *)a.buf[0], *const ring1 = (T *)a.buf[1], *const ring2 = (T *)a.buf[2];
+    const T *__restrict__ wv = wsel<T>(a);
+    const bool fp64 = sizeof(T) == 8;
+    const T g = (T)a.g;
+    const float inv_gf = 1.0f / (float)a.g;
+    const double inv_gd = 1.0 / a.g;
+
+    // ---------------------------------------------------------- start phase
+    // y_0 (and g - d_i for the FP64 form); then one blocking reduction.
+    {
+        const T *cb = nullptr;
+        double cmu = 0.0, cinv = 0.0;
+        if (a.start == 1) {
+            cb = (const T *)a.cbuf[a.cres->buf];
+            cmu = a.cres->mu;
+            cinv = a.cres->inv_s;
+        }
+        Acc<float> acc;   // start sums in float-float (A, B)
+        acc.reset();
+        for (int i = r0 + tid; i < r1; i += blockDim.x) {
+            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
+            ring0[i] = xt;
+            if (fp64) {
+                double d = 0.0;
+                for (int e = __ldg(a.rp + i), e1 = __ldg(a.rp + i + 1); e < e1; e++) d += __ldg(a.w + e);
+                a.gd[i] = a.g - d;
+            }
+            const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
+            acc.A = ff_add(acc.A, v);
+            acc.B = ff_add(acc.B, ff_mul(v, v));
+        }
+        Part p = warp_sum_part(acc.get());
+        if (lane == 0) s_pw[warp] = p;
+        __syncthreads();
+        if (warp == 0) {
+            Part q = (lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + (size_t)blockIdx.x * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+    }
+    if (!grid_sync(gs)) return;
+    Ctl c;
+    if (warp == 0) {
+        Part q = part_zero();
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const ff *src = a.partials + (size_t)b * 3;
+            Part t;
+            t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+            t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+            t.C = ff_zero();
+            q = part_add(q, t);
+        }
+        q = warp_sum_part(q);
+        const double mu0 = to_d(q.A) / (double)n;
+        double ss0 = to_d(q.B) - (double)n * mu0 * mu0;
+        if (ss0 < 0.0) ss0 = 0.0;
+        const int e0 = start_exponent(ss0);
+        ctl_init(c, a, mu0, ss0, e0);
+        if (lane == 0) {
+            s_slot[1] = slot_make(ff_from_double(mu0), e0);  // sweep 1: exact mean of y_0
+            s_slot[0] = slot_make(ff_zero(), 0);             // sweep 2: m_1 = 0
+        }
+    }
+    __syncthreads();
+
+    const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
+    int s = 0;
+    int exit_kind = no_sweeps ? 2 : 0;   // 1: decided stop, 2: count exit
+    while (!no_sweeps) {
+        const Slot sl = s_slot[(s + 1) & 1];
+        if (sl.stop) {
+            exit_kind = 1;
+            break;
+        }
+        if ((a.mode == 1 && s >= a.k_fixed) || (a.mode == 0 && s >= a.max_sweeps)) {
+            exit_kind = 2;
+            break;
+        }
+        const T *x = pick3<T *>(ring0, ring1, ring2, s % 3);
+        T *y = pick3<T *>(ring0, ring1, ring2, (s + 1) % 3);
+        if (warp == 0) {
+            // ---- control: reduce sweep s over all CTAs, decide, plan sweep s+2
+            if (s >= 1) {
+                Part q = part_zero();
+                const ff *base = a.partials + (size_t)(s & 1) * gridDim.x * 3;
+                for (int b = lane; b < (int)gridDim.x; b += 32) {
+                    const ff *src = base + (size_t)b * 3;
+                    Part t;
+                    t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                    t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                    t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                    q = part_add(q, t);
+                }
+                q = warp_sum_part(q);
+                Slot nx;
+                ctrl_step(a, s, q, c, &nx, false);
+                if (lane == 0) s_slot[s & 1] = nx;
+            }
+        } else {
+            // ---- rows of sweep s+1
+            const int rt = tid - 32;
+            const T m = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
+            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
+            const T gm = g * m;
+            Acc<T> acc;
+            acc.reset();
+            for (int t = tb; t < te; t++) {
+                const int t0 = a.tile_row[t], t1 = a.tile_row[t + 1];
+                const int nr = t1 - t0;
+                if (nr <= 0) continue;
+                const int e0 = __ldg(a.rp + t0);
+                const int ne = __ldg(a.rp + t1) - e0;
+                for (int k = rt; k < nr; k += kRowThreads) {
+                    s_rp[k] = __ldg(a.rp + t0 + k) - e0;
+                    s_x[k] = LDXG(x + t0 + k);
+                    s_acc[k] = (T)0;
+                }
+                if (rt == 0) s_rp[nr] = ne;
+                bar_rows(kRowThreads);
+                for (int c0 = 0; c0 < ne; c0 += kChunk) {
+                    const int cn = min(kChunk, ne - c0);
+                    if (!fp64) {
+                        for (int r = rt; r < nr; r += kRowThreads) {
+                            const int lo = max(s_rp[r], c0), hi = min(s_rp[r + 1], c0 + cn);
+                            for (int q = lo; q < hi; q++) s_row[q - c0] = (unsigned short)r;
+                        }
+                        bar_rows(kRowThreads);
+                    }
+                    int jj[kU];
+                    T ww[kU], xj[kU];
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const int k = rt + u * kRowThreads;
+                        jj[u] = 0;
+                        ww[u] = (T)0;
+                        if (k < cn) {
+                            jj[u] = __ldg(a.col + e0 + c0 + k);
+                            ww[u] = __ldg(wv + e0 + c0 + k);
+                        }
+                    }
+#pragma unroll
+                    for (int u = 0; u < kU; u++) {
+                        const int k = rt + u * kRowThreads;
+                        xj[u] = (T)0;
+                        if (k < cn) xj[u] = LDXG(x + jj[u]);
+                    }
+                    if (fp64) {
+                        double *swv = reinterpret_cast<double *>(&ts);
+                        double *sxj = swv + kChunk;
+#pragma unroll
+                        for (int u = 0; u < kU; u++) {
+                            const int k = rt + u * kRowThreads;
+                            if (k < cn) {
+                                swv[k] = (double)ww[u];
+                                sxj[k] = (double)xj[u];
+                            }
+                        }
+                    } else {
+                        float *sp = reinterpret_cast<float *>(&ts);
+#pragma unroll
+                        for (int u = 0; u < kU; u++) {
+                            const int k = rt + u * kRowThreads;
+                            if (k < cn) sp[k] = (float)ww[u] * ((float)s_x[s_row[k]] - (float)xj[u]);
+                        }
+                    }
+                    bar_rows(kRowThreads);
+                    for (int r = rt; r < nr; r += kRowThreads) {
+                        const int lo = max(s_rp[r], c0), hi = min(s_rp[r + 1], c0 + cn);
+                        T ac = s_acc[r];
+                        if (fp64) {
+                            const double *swv = reinterpret_cast<const double *>(&ts);
+                            const double *sxj = swv + kChunk;
+                            for (int q = lo; q < hi; q++) ac = fma((double)swv[q - c0], (double)sxj[q - c0], (double)ac);
+                        } else {
+                            const float *sp = reinterpret_cast<const float *>(&ts);
+                            for (int q = lo; q < hi; q++) ac += (T)sp[q - c0];
+                        }
+                        s_acc[r] = ac;
+                    }
+                    bar_rows(kRowThreads);
+                }
+                for (int r = rt; r < nr; r += kRowThreads) {
+                    const T xi = s_x[r];
+                    T yv;
+                    if (fp64) yv = (T)((fma(a.gd[t0 + r], (double)xi, (double)s_acc[r]) - (double)gm) * (double)sig);
+                    else yv = (g * (xi - m) - s_acc[r]) * sig;
+                    y[t0 + r] = yv;
+                    acc.add(yv, xi);
+                }
+                bar_rows(kRowThreads);
+            }
+            Part p = warp_sum_part(acc.get());
+            if (lane == 0) s_pw[warp] = p;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Part q = (lane >= 1 && lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + ((size_t)((s + 1) & 1) * gridDim.x + blockIdx.x) * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+        if (!grid_sync(gs)) return;
+        s++;
+    }
+    // ---------------------------------------------------------- result
+    if (warp == 0) {
+        if (exit_kind == 2 && !no_sweeps) {
+            // the last sweep s ended the loop by count: reduce it now
+            Part q = part_zero();
+            const ff *base = a.partials + (size_t)(s & 1) * gridDim.x * 3;
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const ff *src = base + (size_t)b * 3;
+                Part t;
+                t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                q = part_add(q, t);
+            }
+            q = warp_sum_part(q);
+            ctrl_step(a, s, q, c, nullptr, true);
+        }
+        if (blockIdx.x == 0 && lane == 0) {
+            const int rs = c.res_sweep;
+            const int rb = c.zero ? (rs - 1) % 3 : rs % 3;
+            write_result(a, c, rb, (rs + 2) % 3);
+        }
+    }
+}
+
+// ================================================================== small kernel
+// Shared memory: ring[3][n] T, gd[n] (FP64), w[m] T, rp[n+1] int, col[m] int.
+template <typename T>
+constexpr size_t small_smem_bytes(long long n, long long m) {
+    return (size_t)(sizeof(T) * (3 * n + m) + (sizeof(T) == 8 ? 8 * n : 0) + 4 * (n + 1) + 4 * m + 64);
+}
+
+template <typename T, int G>
+__global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, GridSync *) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n;
+    const int m = a.rp[n];
+    const bool fp64 = sizeof(T) == 8;
+    T *ring0 = reinterpret_cast<T *>(smem_raw);
+    double *s_gd = reinterpret_cast<double *>(ring0 + 3 * n);
+    T *s_w = fp64 ? reinterpret_cast<T *>(s_gd + n) : ring0 + 3 * n;
+    int *s_rp = reinterpret_cast<int *>(s_w + m);
+    int *s_col = s_rp + n + 1;
+    __shared__ Part s_pw[2][32];
+    __shared__ Slot s_slot[2];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nw = blockDim.x >> 5;
+    const T *__restrict__ wv = wsel<T>(a);
+    const T g = (T)a.g;
+    const float inv_gf = 1.0f / (float)a.g;
+    const double inv_gd = 1.0 / a.g;
+
+    for (int i = tid; i <= n; i += blockDim.x) s_rp[i] = a.rp[i];
+    for (int e = tid; e < m; e += blockDim.x) {
+        s_col[e] = a.col[e];
+        s_w[e] = wv[e];
+    }
+    {
+        const T *cb = nullptr;
+        double cmu = 0.0, cinv = 0.0;
+        if (a.start == 1) {
+            cb = (const T *)a.cbuf[a.cres->buf];
+            cmu = a.cres->mu;
+            cinv = a.cres->inv_s;
+        }
+        Acc<float> acc;
+        acc.reset();
+        for (int i = tid; i < n; i += blockDim.x) {
+            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
+            ring0[i] = xt;
+            if (fp64) {
+                double d = 0.0;
+                for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
+                s_gd[i] = a.g - d;
+            }
+            const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
+            acc.A = ff_add(acc.A, v);
+            acc.B = ff_add(acc.B, ff_mul(v, v));
+        }
+        Part p = warp_sum_part(acc.get());
+        if (lane == 0) s_pw[0][warp] = p;
+    }
+    __syncthreads();
+    Ctl c;
+    if (warp == 0) {
+        Part q = (lane < nw) ? s_pw[0][lane] : part_zero();
+        q = warp_sum_part(q);
+        const double mu0 = to_d(q.A) / (double)n;
+        double ss0 = to_d(q.B) - (double)n * mu0 * mu0;
+        if (ss0 < 0.0) ss0 = 0.0;
+        const int e0 = start_exponent(ss0);
+        ctl_init(c, a, mu0, ss0, e0);
+        if (lane == 0) {
+            s_slot[1] = slot_make(ff_from_double(mu0), e0);
+            s_slot[0] = slot_make(ff_zero(), 0);
+        }
+    }
+    __syncthreads();
+
+    const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
+    int s = 0;
+    int exit_kind = no_sweeps ? 2 : 0;
+    const int rt = tid - 32, nrt = blockDim.x - 32;
+    const int rlane = rt & (G - 1);
+    const int groups = nrt / G;
+    while (!no_sweeps) {
+        const Slot sl = s_slot[(s + 1) & 1];
+        if (sl.stop) {
+            exit_kind = 1;
+            break;
+        }
+        if ((a.mode == 1 && s >= a.k_fixed) || (a.mode == 0 && s >= a.max_sweeps)) {
+            exit_kind = 2;
+            break;
+        }
+        const T *x = ring0 + (size_t)(s % 3) * n;
+        T *y = ring0 + (size_t)((s + 1) % 3) * n;
+        if (warp == 0) {
+            if (s >= 1) {
+                Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
+                q = warp_sum_part(q);
+                Slot nx;
+                ctrl_step(a, s, q, c, &nx, false);
+                if (lane == 0) s_slot[s & 1] = nx;
+            }
+        } else {
+            const T mT = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
+            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
+            const T gm = g * mT;
+            Acc<T> acc;
+            acc.reset();
+            for (int base = rt / G;; base += groups) {
+                if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
+                const int i = base;
+                T ac = (T)0, xi = (T)0;
+                if (i < n) {
+                    xi = x[i];
+                    if (fp64) {
+                        for (int e = s_rp[i] + rlane, e1 = s_rp[i + 1]; e < e1; e += G)
+                            ac = fma(s_w[e], x[s_col[e]], ac);
+                    } else {
+                        for (int e = s_rp[i] + rlane, e1 = s_rp[i + 1]; e < e1; e += G)
+                            ac += s_w[e] * (xi - x[s_col[e]]);
+                    }
+                }
+                ac = group_sum<G>(ac);
+                if (i < n && rlane == 0) {
+                    T yv;
+                    if (fp64) yv = (T)((fma(s_gd[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
+                    else yv = (g * (xi - mT) - ac) * sig;
+                    y[i] = yv;
+                    acc.add(yv, xi);
+                }
+            }
+            Part p = warp_sum_part(acc.get());
+            if (lane == 0) s_pw[(s + 1) & 1][warp] = p;
+        }
+        __syncthreads();
+        s++;
+    }
+    __shared__ int s_rb, s_rbp;
+    if (warp == 0) {
+        if (exit_kind == 2 && !no_sweeps) {
+            Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
+            q = warp_sum_part(q);
+            ctrl_step(a, s, q, c, nullptr, true);
+        }
+        if (lane == 0) {
+            const int rs = c.res_sweep;
+            s_rb = c.zero ? (rs + 2) % 3 : rs % 3;
+            s_rbp = (rs + 2) % 3;
+            write_result(a, c, 0, 1);
+        }
+    }
+    __syncthreads();
+    // result -> buf[0], previous iterate -> buf[1]
+    T *o0 = (T *)a.buf[0], *o1 = (T *)a.buf[1];
+    const T *rr = ring0 + (size_t)s_rb * n, *rp = ring0 + (size_t)s_rbp * n;
+    for (int i = tid; i < n; i += blockDim.x) {
+        o0[i] = rr[i];
+        o1[i] = rp[i];
+    }
+}
+
+// ================================================================== host side
+__global__ void k_tiles(int n, const int *__restrict__ rp, int ntiles, int *__restrict__ tile_row) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= ntiles; k += gridDim.x * blockDim.x) {
+        if (k == ntiles) {
+            tile_row[k] = n;
+            continue;
+        }
+        const long long target = (long long)k * kTileCost;
+        int lo = 0, hi = n;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((long long)rp[mid] + 4ll * mid < target) lo = mid + 1;
+            else hi = mid;
+        }
+        tile_row[k] = lo;
+    }
+}
+
+int tile_count(int n, long long nnz) { return (int)((nnz + 4ll * n + kTileCost - 1) / kTileCost); }
+
+cmg_status_t build_tiles(int n, long long nnz, const int *rp, int *tile_row, cudaStream_t s) {
+    const int nt = tile_count(n, nnz);
+    k_tiles<<<grid_for(nt + 1, 256), 256, 0, s>>>(n, rp, nt, tile_row);
+    return launch_status();
+}
+
+static size_t tiled_smem(bool fp32) {
+    const size_t e = fp32 ? sizeof(float) : sizeof(double);
+    const size_t ts = fp32 ? sizeof(TileSmem<float>) : sizeof(TileSmem<double>);
+    return ts + e * 2 * kTileRows + sizeof(int) * (kTileRows + 4) + 2 * kChunk;
+}
+
+template <typename T>
+static const void *small_kernel(int G) {
+    switch (G) {
+        case 1: return (const void *)k_power_small<T, 1>;
+        case 2: return (const void *)k_power_small<T, 2>;
+        case 4: return (const void *)k_power_small<T, 4>;
+        case 8: return (const void *)k_power_small<T, 8>;
+        case 16: return (const void *)k_power_small<T, 16>;
+        default: return (const void *)k_power_small<T, 32>;
+    }
+}
+
+// Lanes per row in the small kernel: about 4 entries per lane, fewer lanes
+// when that leaves more row groups than rows would need.
+static int small_lanes(int n, long long nnz, int fp32) {
+    const double avg = (double)nnz / (double)std::max(1, n);
+    int g = 1;
+    if (fp32) {
+        // a row per lane while rows are short: every extra lane costs a share
+        // of the per-sweep float-float reduction
+        while (g < 32 && g * 24 < avg) g <<= 1;
+    } else {
+        // FP64: every lane-operation costs FP64 issue slots, so use the fewest
+        // lanes that keep each lane's dependent FMA chain to about 8 entries
+        while (g < 32 && g * 8 < avg) g <<= 1;
+    }
+    return g;
+}
+
+// Threads of the small kernel: the control warp plus enough row warps for
+// one row per lane group (at most 31 row warps).
+static int small_threads(int n, int G) {
+    long long lanes = (long long)n * G;
+    int w = (int)std::min<long long>(31, std::max<long long>(1, (lanes + 31) / 32));
+    return 32 * (w + 1);
+}
+
+bool small_level_fits(int n, long long nnz, int fp32) {
+    DeviceInfo d;
+    if (device_info(&d) != CMG_OK) return false;
+    const size_t b = fp32 ? small_smem_bytes<float>(n, nnz) : small_smem_bytes<double>(n, nnz);
+    return b + 4096 <= (size_t)d.max_smem_optin;
+}
+
+cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
+    const PiLevel &lv = *run.lv;
+    Scratch scr(s);
+    PiArgs a;
+    a.n = lv.n;
+    a.rp = lv.rp;
+    a.col = lv.col;
+    a.w = lv.w;
+    a.w32 = lv.w32;
+    a.g = lv.g;
+    a.tile_row = lv.tile_row;
+    a.ntiles = lv.ntiles;
+    a.mode = run.mode;
+    a.k_fixed = run.k_fixed;
+    a.max_sweeps = run.max_sweeps;
+    a.tol = run.tol;
+    a.seed = run.seed;
+    a.start = run.x_init ? 2 : (run.coarse_res ? 1 : 0);
+    for (int k = 0; k < 3; k++) {
+        a.cbuf[k] = run.coarse_bufs[k];
+        a.buf[k] = run.bufs[k];
+    }
+    a.cres = run.coarse_res;
+    a.agg = run.coarse_agg;
+    a.x_init = run.x_init;
+    a.gd = run.gd;
+    a.res = run.res;
+    a.partials = nullptr;
+    void *args[] = {&a, &gs};
+    if (small_level_fits(lv.n, lv.nnz, run.fp32)) {
+        const int G = small_lanes(lv.n, lv.nnz, run.fp32);
+        const void *kern = run.fp32 ? small_kernel<float>(G) : small_kernel<double>(G);
+        const size_t smem = run.fp32 ? small_smem_bytes<float>(lv.n, lv.nnz)
+                                     : small_smem_bytes<double>(lv.n, lv.nnz);
+        CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        return coop_launch(kern, 1, small_threads(lv.n, G), smem, s, args, gs);
+    }
+    if (!run.fp32 && !run.gd) return CMG_ERR_INVALID_ARG;
+    if (!a.tile_row) {
+        int *tr;
+        if (ws) {
+            if (tile_count(lv.n, lv.nnz) + 1 > ws->tile_cap) return CMG_ERR_TOO_LARGE;
+            tr = ws->tile_row;
+        } else {
+            CMG_TRY(scr.get(&tr, (size_t)tile_count(lv.n, lv.nnz) + 1));
+        }
+        CMG_TRY(build_tiles(lv.n, lv.nnz, lv.rp, tr, s));
+        a.tile_row = tr;
+        a.ntiles = tile_count(lv.n, lv.nnz);
+    }
+    const void *kern = run.fp32 ? (const void *)k_power_tiled<float> : (const void *)k_power_tiled<double>;
+    const size_t smem = tiled_smem(run.fp32 != 0);
+    CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int maxb = 0;
+    CMG_TRY(coop_max_blocks(kern, kTileThreads, smem, &maxb));
+    // one tile per CTA where possible (each tile's phases are latency-bound),
+    // never more CTAs than co-resident
+    const int blocks = std::max(1, std::min(maxb, a.ntiles));
+    // partial sums: [2][blocks][3] float-float values (6 floats = 3 doubles each)
+    double *partials;
+    if (ws) {
+        if (2 * blocks * 3 > ws->partials_cap) return CMG_ERR_TOO_LARGE;
+        partials = ws->partials;
+    } else {
+        CMG_TRY(scr.get(&partials, (size_t)2 * blocks * 3));
+    }
+    a.partials = reinterpret_cast<ff *>(partials);
+    return coop_launch(kern, blocks, kTileThreads, smem, s, args, gs);
+}
+
 // Sum of K per-thread doubles over the CTA, result in out[] of every thread
-// (fixed order).  sm: 32*K doubles.  Two __syncthreads.
+// (fixed order).  sm: 32*K doubles.  Two __syncthreads.  (Used once per
+// solve by the final pass.)
 template <int K>
 __device__ __forceinline__ void block_allsum(double (&v)[K], double *sm, double (&out)[K]) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -185,390 +952,6 @@ __device__ __forceinline__ bool grid_allsum(double (&v)[K], double *sm, double *
     return true;
 }
 
-template <typename T>
-__device__ __forceinline__ const T *wsel(const PiArgs &a);
-template <>
-__device__ __forceinline__ const double *wsel<double>(const PiArgs &a) { return a.w; }
-template <>
-__device__ __forceinline__ const float *wsel<float>(const PiArgs &a) { return a.w32; }
-
-// ================================================================== tiled kernel
-template <typename T>
-__global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridSync *gs) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *s_prod = reinterpret_cast<T *>(smem_raw);                       // kChunk
-    T *s_x = s_prod + kChunk;                                         // kTileRows
-    T *s_acc = s_x + kTileRows;                                       // kTileRows
-    int *s_rp = reinterpret_cast<int *>(s_acc + kTileRows);           // kTileRows + 1
-    unsigned short *s_row = reinterpret_cast<unsigned short *>(s_rp + kTileRows + 4);  // kChunk
-    __shared__ double sm[32 * kNumPartials];
-
-    const int n = a.n;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const int tb = (int)((long long)a.ntiles * blockIdx.x / gridDim.x);
-    const int te = (int)((long long)a.ntiles * (blockIdx.x + 1) / gridDim.x);
-    const int r0 = a.tile_row[tb], r1 = a.tile_row[te];
-    T *buf0 = (T *)a.buf0, *buf1 = (T *)a.buf1;
-    const T *__restrict__ wv = wsel<T>(a);
-    double *part0 = a.partials;
-    double *part1 = a.partials + (size_t)gridDim.x * kNumPartials;
-
-    // ---- start vector into buf0; Gram-Schmidt against 1; norm
-    double p[kNumPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double S[kNumPartials];
-    {
-        const T *cb = nullptr;
-        double cmu = 0.0, cinv = 0.0;
-        if (a.start == 1) {
-            cb = (const T *)(a.cres->buf ? a.cbuf1 : a.cbuf0);
-            cmu = a.cres->mu;
-            cinv = a.cres->inv_s;
-        }
-        for (int i = r0 + tid; i < r1; i += nt) {
-            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
-            buf0[i] = xt;
-            p[0] += (double)xt;
-        }
-    }
-    if (!grid_allsum<kNumPartials>(p, sm, part0, S, gs)) return;
-    const double mu0 = S[0] / (double)n;
-    p[0] = 0.0;
-    for (int i = r0 + tid; i < r1; i += nt) {
-        const double d = (double)buf0[i] - mu0;
-        p[0] += d * d;
-    }
-    if (!grid_allsum<kNumPartials>(p, sm, part1, S, gs)) return;
-    SweepState st;
-    st.mu = mu0;
-    st.inv_s = S[0] > 0.0 ? 1.0 / sqrt(S[0]) : 0.0;
-    st.mu_prev = st.mu;
-    st.inv_prev = st.inv_s;
-    st.cosv = 0.0;
-    st.cur = 0;
-    st.k = 0;
-    st.zero = 0;
-    const bool run = !(a.mode == 1 && a.k_fixed <= 0);
-    const T gT = (T)a.g;
-    constexpr int U = kChunk / kTileThreads;
-
-    while (run) {
-        const T *x = st.cur ? buf1 : buf0;
-        T *y = st.cur ? buf0 : buf1;
-        const T muT = (T)st.mu, invT = (T)st.inv_s;
-        const double mu = st.mu, inv_s = st.inv_s;
-#pragma unroll
-        for (int q = 0; q < kNumPartials; q++) p[q] = 0.0;
-        for (int t = tb; t < te; t++) {
-            const int t0 = a.tile_row[t], t1 = a.tile_row[t + 1];
-            const int nr = t1 - t0;
-            if (nr <= 0) continue;
-            const int e0 = __ldg(a.rp + t0);
-            const int ne = __ldg(a.rp + t1) - e0;
-            for (int k = tid; k < nr; k += nt) {
-                s_rp[k] = __ldg(a.rp + t0 + k) - e0;
-                s_x[k] = LDX(x + t0 + k);
-                s_acc[k] = (T)0;
-            }
-            if (tid == 0) s_rp[nr] = ne;
-            __syncthreads();
-            for (int c0 = 0; c0 < ne; c0 += kChunk) {
-                const int cn = min(kChunk, ne - c0);
-                // row of every entry of the chunk
-                for (int r = tid; r < nr; r += nt) {
-                    const int lo = max(s_rp[r], c0), hi = min(s_rp[r + 1], c0 + cn);
-                    for (int q = lo; q < hi; q++) s_row[q - c0] = (unsigned short)r;
-                }
-                __syncthreads();
-                // products w_ij (x_i - x_j): all loads of the chunk issued first
-                int jj[U];
-                T ww[U], xj[U];
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int k = tid + u * kTileThreads;
-                    jj[u] = 0;
-                    ww[u] = (T)0;
-                    if (k < cn) {
-                        jj[u] = __ldg(a.col + e0 + c0 + k);
-                        ww[u] = __ldg(wv + e0 + c0 + k);
-                    }
-                }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int k = tid + u * kTileThreads;
-                    xj[u] = (T)0;
-                    if (k < cn) xj[u] = LDX(x + jj[u]);
-                }
-#pragma unroll
-                for (int u = 0; u < U; u++) {
-                    const int k = tid + u * kTileThreads;
-                    if (k < cn) s_prod[k] = ww[u] * (s_x[s_row[k]] - xj[u]);
-                }
-                __syncthreads();
-                // per-row sums, left to right
-                for (int r = tid; r < nr; r += nt) {
-                    const int lo = max(s_rp[r], c0), hi = min(s_rp[r + 1], c0 + cn);
-                    T acc = s_acc[r];
-                    for (int q = lo; q < hi; q++) acc += s_prod[q - c0];
-                    s_acc[r] = acc;
-                }
-                __syncthreads();
-            }
-            for (int r = tid; r < nr; r += nt) {
-                const T xi = s_x[r];
-                const T yv = (gT * (xi - muT) - s_acc[r]) * invT;
-                y[t0 + r] = yv;
-                const double yd = (double)yv;
-                const double xs = ((double)xi - mu) * inv_s;
-                p[0] += yd;
-                p[1] += yd * yd;
-                p[2] += yd * xs;
-                p[3] += xs;
-                p[4] += xs * xs;
-            }
-            __syncthreads();
-        }
-        if (!grid_allsum<kNumPartials>(p, sm, (st.k & 1) ? part1 : part0, S, gs)) return;
-        if (after_sweep(a, S, n, st)) break;
-    }
-    if (blockIdx.x == 0 && tid == 0) write_result(a, st, run);
-}
-
-// ================================================================== small kernel
-// Shared memory: w[m] T, x[n] T, y[n] T, rp[n+1] int, col[m] int.
-template <typename T>
-constexpr size_t small_smem_bytes(long long n, long long m) {
-    return (size_t)(4 * (n + 1) + 4 * m + sizeof(T) * m + 2 * sizeof(T) * n + 64);
-}
-
-template <typename T, int G>
-__global__ void __launch_bounds__(kSmallThreads) k_power_small(PiArgs a, GridSync *) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n;
-    const int m = a.rp[n];
-    T *s_w = reinterpret_cast<T *>(smem_raw);
-    T *s_x0 = s_w + m;
-    T *s_x1 = s_w + m + n;
-    int *s_rp = reinterpret_cast<int *>(s_w + m + 2 * n);
-    int *s_col = s_rp + n + 1;
-    __shared__ double sm[32 * kNumPartials];
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const T *__restrict__ wv = wsel<T>(a);
-
-    for (int i = tid; i <= n; i += nt) s_rp[i] = a.rp[i];
-    for (int e = tid; e < m; e += nt) {
-        s_col[e] = a.col[e];
-        s_w[e] = wv[e];
-    }
-    double p[kNumPartials] = {0.0, 0.0, 0.0, 0.0, 0.0};
-    double S[kNumPartials];
-    {
-        const T *cb = nullptr;
-        double cmu = 0.0, cinv = 0.0;
-        if (a.start == 1) {
-            cb = (const T *)(a.cres->buf ? a.cbuf1 : a.cbuf0);
-            cmu = a.cres->mu;
-            cinv = a.cres->inv_s;
-        }
-        for (int i = tid; i < n; i += nt) {
-            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
-            s_x0[i] = xt;
-            p[0] += (double)xt;
-        }
-    }
-    block_allsum<kNumPartials>(p, sm, S);
-    const double mu0 = S[0] / (double)n;
-    p[0] = 0.0;
-    for (int i = tid; i < n; i += nt) {
-        const double d = (double)s_x0[i] - mu0;
-        p[0] += d * d;
-    }
-    block_allsum<kNumPartials>(p, sm, S);
-    SweepState st;
-    st.mu = mu0;
-    st.inv_s = S[0] > 0.0 ? 1.0 / sqrt(S[0]) : 0.0;
-    st.mu_prev = st.mu;
-    st.inv_prev = st.inv_s;
-    st.cosv = 0.0;
-    st.cur = 0;
-    st.k = 0;
-    st.zero = 0;
-    const bool run = !(a.mode == 1 && a.k_fixed <= 0);
-    const T gT = (T)a.g;
-    const int lane = tid & (G - 1);
-    const int groups = nt / G;
-    while (run) {
-        const T *x = st.cur ? s_x1 : s_x0;
-        T *y = st.cur ? s_x0 : s_x1;
-        const T muT = (T)st.mu, invT = (T)st.inv_s;
-        const double mu = st.mu, inv_s = st.inv_s;
-#pragma unroll
-        for (int q = 0; q < kNumPartials; q++) p[q] = 0.0;
-        for (int base = tid / G;; base += groups) {
-            if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
-            const int i = base;
-            T acc = (T)0, xi = (T)0;
-            if (i < n) {
-                xi = x[i];
-                for (int e = s_rp[i] + lane, e1 = s_rp[i + 1]; e < e1; e += G)
-                    acc += s_w[e] * (xi - x[s_col[e]]);
-            }
-            acc = group_sum<G>(acc);
-            if (i < n && lane == 0) {
-                const T yv = (gT * (xi - muT) - acc) * invT;
-                y[i] = yv;
-                const double yd = (double)yv;
-                const double xs = ((double)xi - mu) * inv_s;
-                p[0] += yd;
-                p[1] += yd * yd;
-                p[2] += yd * xs;
-                p[3] += xs;
-                p[4] += xs * xs;
-            }
-        }
-        block_allsum<kNumPartials>(p, sm, S);
-        if (after_sweep(a, S, n, st)) break;
-    }
-    // result -> buf0, previous iterate -> buf1 (for the FP64 final recompute)
-    T *out0 = (T *)a.buf0, *out1 = (T *)a.buf1;
-    const T *res = st.cur ? s_x1 : s_x0;
-    const T *prv = st.cur ? s_x0 : s_x1;
-    for (int i = tid; i < n; i += nt) {
-        out0[i] = res[i];
-        out1[i] = prv[i];
-    }
-    if (tid == 0) {
-        SweepState r = st;
-        r.cur = 0;
-        write_result(a, r, run);
-    }
-}
-
-// ================================================================== host side
-__global__ void k_tiles(int n, const int *__restrict__ rp, int ntiles, int *__restrict__ tile_row) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= ntiles; k += gridDim.x * blockDim.x) {
-        if (k == ntiles) {
-            tile_row[k] = n;
-            continue;
-        }
-        const long long target = (long long)k * kTileCost;
-        int lo = 0, hi = n;
-        while (lo < hi) {
-            const int mid = (lo + hi) >> 1;
-            if ((long long)rp[mid] + 4ll * mid < target) lo = mid + 1;
-            else hi = mid;
-        }
-        tile_row[k] = lo;
-    }
-}
-
-int tile_count(int n, long long nnz) { return (int)((nnz + 4ll * n + kTileCost - 1) / kTileCost); }
-
-cmg_status_t build_tiles(int n, long long nnz, const int *rp, int *tile_row, cudaStream_t s) {
-    const int nt = tile_count(n, nnz);
-    k_tiles<<<grid_for(nt + 1, 256), 256, 0, s>>>(n, rp, nt, tile_row);
-    return launch_status();
-}
-
-static size_t tiled_smem(bool fp32) {
-    const size_t e = fp32 ? sizeof(float) : sizeof(double);
-    return e * (kChunk + 2 * kTileRows) + sizeof(int) * (kTileRows + 4) + 2 * kChunk;
-}
-
-template <typename T>
-static const void *small_kernel(int G) {
-    switch (G) {
-        case 1: return (const void *)k_power_small<T, 1>;
-        case 2: return (const void *)k_power_small<T, 2>;
-        case 4: return (const void *)k_power_small<T, 4>;
-        case 8: return (const void *)k_power_small<T, 8>;
-        case 16: return (const void *)k_power_small<T, 16>;
-        default: return (const void *)k_power_small<T, 32>;
-    }
-}
-
-// Lanes per row in the small kernel: about 4 entries per lane, and one row
-// per lane group when the level has at most kSmallThreads / G rows.
-static int small_lanes(int n, long long nnz) {
-    const double avg = (double)nnz / (double)std::max(1, n);
-    int g = 1;
-    while (g < 32 && g * 4 < avg) g <<= 1;
-    while (g > 1 && (long long)(kSmallThreads / g) < n) g >>= 1;
-    return g;
-}
-
-bool small_level_fits(int n, long long nnz, int fp32) {
-    DeviceInfo d;
-    if (device_info(&d) != CMG_OK) return false;
-    const size_t b = fp32 ? small_smem_bytes<float>(n, nnz) : small_smem_bytes<double>(n, nnz);
-    return b + 32 * kNumPartials * 8 + 256 <= (size_t)d.max_smem_optin;
-}
-
-cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
-    const PiLevel &lv = *run.lv;
-    Scratch scr(s);
-    PiArgs a;
-    a.n = lv.n;
-    a.rp = lv.rp;
-    a.col = lv.col;
-    a.w = lv.w;
-    a.w32 = lv.w32;
-    a.g = lv.g;
-    a.tile_row = lv.tile_row;
-    a.ntiles = lv.ntiles;
-    a.mode = run.mode;
-    a.k_fixed = run.k_fixed;
-    a.max_sweeps = run.max_sweeps;
-    a.tol = run.tol;
-    a.seed = run.seed;
-    a.start = run.x_init ? 2 : (run.coarse_res ? 1 : 0);
-    a.cbuf0 = run.coarse_buf;
-    a.cbuf1 = run.coarse_buf1;
-    a.cres = run.coarse_res;
-    a.agg = run.coarse_agg;
-    a.x_init = run.x_init;
-    a.buf0 = run.bufs[0];
-    a.buf1 = run.bufs[1];
-    a.res = run.res;
-    a.partials = nullptr;
-    void *args[] = {&a, &gs};
-    if (small_level_fits(lv.n, lv.nnz, run.fp32)) {
-        const int G = small_lanes(lv.n, lv.nnz);
-        const void *kern = run.fp32 ? small_kernel<float>(G) : small_kernel<double>(G);
-        const size_t smem = run.fp32 ? small_smem_bytes<float>(lv.n, lv.nnz)
-                                     : small_smem_bytes<double>(lv.n, lv.nnz);
-        CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        return coop_launch(kern, 1, kSmallThreads, smem, s, args, gs);
-    }
-    if (!a.tile_row) {
-        int *tr;
-        if (ws) {
-            if (tile_count(lv.n, lv.nnz) + 1 > ws->tile_cap) return CMG_ERR_TOO_LARGE;
-            tr = ws->tile_row;
-        } else {
-            CMG_TRY(scr.get(&tr, (size_t)tile_count(lv.n, lv.nnz) + 1));
-        }
-        CMG_TRY(build_tiles(lv.n, lv.nnz, lv.rp, tr, s));
-        a.tile_row = tr;
-        a.ntiles = tile_count(lv.n, lv.nnz);
-    }
-    const void *kern = run.fp32 ? (const void *)k_power_tiled<float> : (const void *)k_power_tiled<double>;
-    const size_t smem = tiled_smem(run.fp32 != 0);
-    CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    int maxb = 0;
-    CMG_TRY(coop_max_blocks(kern, kTileThreads, smem, &maxb));
-    // at least 4 tiles per CTA where possible, never more CTAs than co-resident
-    int blocks = std::max(1, std::min(maxb, (a.ntiles + 3) / 4));
-    double *partials;
-    if (ws) {
-        if (2 * blocks * kNumPartials > ws->partials_cap) return CMG_ERR_TOO_LARGE;
-        partials = ws->partials;
-    } else {
-        CMG_TRY(scr.get(&partials, (size_t)2 * blocks * kNumPartials));
-    }
-    a.partials = partials;
-    return coop_launch(kern, blocks, kTileThreads, smem, s, args, gs);
-}
-
 // ================================================================== finalisation
 // Rows [r0, r1) of CTA b out of nb, balanced by 3 * nnz + 5 * rows.
 __device__ __forceinline__ void cta_rows(const int *rp, int n, int b, int nb, int *r0, int *r1) {
@@ -593,8 +976,7 @@ struct FinArgs {
     const double *w;
     double g;
     int fp32;
-    const void *buf0;
-    const void *buf1;
+    const void *buf[3];
     const PiResult *res;
     double *u;
     double *tmp;
@@ -628,7 +1010,7 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinArgs a, GridSync *g
         const bool recompute = a.fp32 && r.sweeps > 0 && !r.zero;
         if (recompute) {
             // FP64 recomputation of the last sweep from the previous (FP32) iterate
-            const float *x = (const float *)(r.buf ? a.buf0 : a.buf1);
+            const float *x = (const float *)a.buf[r.buf_prev];
             p[0] = p[1] = p[2] = p[3] = 0.0;
             for (int base = r0 + threadIdx.x / G;; base += groups) {
                 if (__shfl_sync(0xffffffffu, base, 0) >= r1) break;
@@ -656,11 +1038,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinArgs a, GridSync *g
             const double inv = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a.u[i] = (a.tmp[i] - mu) * inv;
         } else if (a.fp32) {
-            const float *y = (const float *)(r.buf ? a.buf1 : a.buf0);
+            const float *y = (const float *)a.buf[r.buf];
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
                 a.u[i] = ((double)y[i] - r.mu) * r.inv_s;
         } else {
-            const double *y = (const double *)(r.buf ? a.buf1 : a.buf0);
+            const double *y = (const double *)a.buf[r.buf];
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a.u[i] = (y[i] - r.mu) * r.inv_s;
         }
     }
@@ -787,9 +1169,9 @@ static const void *finalize_kernel(int G) {
     }
 }
 
-cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void *buf1,
-                      const PiResult *res, double *u, int sign, int fresh, double *out2,
-                      GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
+cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const PiResult *res,
+                      double *u, int sign, int fresh, double *out2, GridSync *gs, cudaStream_t s,
+                      const PiWorkspace *ws) {
     const int G = lanes_for_avg((double)lv.nnz / (double)std::max(1, lv.n));
     const void *kern = finalize_kernel(G);
     int maxb = 0;
@@ -815,8 +1197,7 @@ cmg_status_t finalize(const PiLevel &lv, int fp32, const void *buf0, const void 
     a.w = lv.w;
     a.g = lv.g;
     a.fp32 = fp32;
-    a.buf0 = buf0;
-    a.buf1 = buf1;
+    for (int k = 0; k < 3; k++) a.buf[k] = bufs ? bufs[k] : nullptr;
     a.res = res;
     a.u = u;
     a.tmp = tmp;
