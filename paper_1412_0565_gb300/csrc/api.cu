@@ -88,6 +88,7 @@ struct LevelData {
     int *agg = nullptr;  // onto the next level
     int *tiles = nullptr;
     int ntiles = 0;
+    long long sell_nnz = 0;
     double g = 0.0;
 };
 
@@ -260,11 +261,16 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
             }
         }
     }
-    // ---- row tiles of every level for the sweep kernel
-    for (auto &L : h->lv) {
-        L.ntiles = tile_count(L.n, L.nnz);
-        CMG_TRY(dev_alloc_n(&L.tiles, (size_t)L.ntiles + 1, s));
-        CMG_TRY(build_tiles(L.n, L.nnz, L.rp, L.tiles, s));
+    // ---- row tiles (large levels) and SELL-32 sizes (small levels)
+    {
+        unsigned long long *cnt;
+        CMG_TRY(scr.get(&cnt, 1));
+        for (auto &L : h->lv) {
+            L.ntiles = tile_count(L.n, L.nnz);
+            CMG_TRY(dev_alloc_n(&L.tiles, (size_t)L.ntiles + 1, s));
+            CMG_TRY(build_tiles(L.n, L.nnz, L.rp, L.tiles, s));
+            if (L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
+        }
     }
     // ---- solve workspace: a buffer pair per level, results, barrier state
     const size_t esz = (o.precision == CMG_PRECISION_FP32_SWEEP) ? sizeof(float) : sizeof(double);
@@ -375,6 +381,7 @@ static PiLevel level_view(const LevelData &L) {
     v.agg = L.agg;
     v.tile_row = L.tiles;
     v.ntiles = L.ntiles;
+    v.sell_nnz = L.sell_nnz;
     return v;
 }
 

@@ -60,6 +60,15 @@ __device__ __forceinline__ ff ff_add_f(ff a, float b) {
     return fast_two_sum(s.hi, e);
 }
 
+// Sum without the final renormalisation (hi + lo is still exact up to the
+// rounding of the lo additions); renormalise with ff_norm when done.
+__device__ __forceinline__ ff ff_add_lazy(ff a, ff b) {
+    const ff s = two_sum(a.hi, b.hi);
+    return ff_make(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ ff ff_norm(ff a) { return fast_two_sum(a.hi, a.lo); }
+
 __device__ __forceinline__ ff ff_neg(ff a) { return ff_make(-a.hi, -a.lo); }
 
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }

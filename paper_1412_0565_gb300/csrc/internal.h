@@ -73,7 +73,13 @@ struct PiLevel {
     const int *agg;      // this level -> next coarser level (nullptr at the coarsest)
     const int *tile_row; // row tiles of the sweep kernel (nullptr: built on demand)
     int ntiles;
+    long long sell_nnz;  // SELL-32 size for the shared-memory kernel (0: unknown)
 };
+
+// SELL-32 size of a CSR level (sum over 32-row slices of 32 x longest row);
+// dev_counter: one device unsigned long long of scratch.  Synchronises s.
+cmg_status_t sell_size(int n, const int *rp, unsigned long long *dev_counter, long long *out,
+                       cudaStream_t s);
 
 // Row tiles of a level for the tiled sweep kernel (tile_count + 1 entries).
 int tile_count(int n, long long nnz);

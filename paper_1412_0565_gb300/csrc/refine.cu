@@ -39,6 +39,15 @@
 
 namespace cmg {
 
+#ifdef CMG_TRACE
+// cycle stamps of the first sweeps of the last small-kernel launch:
+// [sweep][0] loop top, [1] control done, [2] first row warp done, [3] last row warp done
+__device__ long long g_trace[256][8];
+#define TRACE(s, k) do { if ((s) < 256) g_trace[(s)][(k)] = clock64(); } while (0)
+#else
+#define TRACE(s, k) do { } while (0)
+#endif
+
 // Loads of data written by other CTAs of the same launch go through L2.
 #define LDX(p) __ldcg(p)
 // Gathers of the iterate: ordinary (L1-cached) loads.  The iterate read in a
@@ -59,7 +68,8 @@ constexpr int kTileRows = 960;
 constexpr int kTileCost = 3840;                   // entries + 4 * rows per tile
 constexpr int kSmallMaxThreads = 1024;
 constexpr int kFinThreads = 256;
-constexpr float kZeroTol2f = 2.0194839e-28f;  // (64 eps_64)^2
+constexpr float kZeroTol2_64 = 2.0194839e-28f;  // (64 eps_64)^2
+constexpr float kZeroTol2_32 = 5.8207661e-11f;  // (64 eps_32)^2
 
 struct PiArgs {
     int n;
@@ -84,6 +94,8 @@ struct PiArgs {
     double *gd;             // FP64 form: g - d_i
     PiResult *res;
     ff *partials;           // [2][gridDim.x][3] (tiled kernel)
+    float zero_tol2;        // (64 eps)^2 of the sweep precision
+    long long sell_nnz;     // SELL-32 size of the level (0: unknown)
 };
 
 __device__ __forceinline__ uint64_t sm64(uint64_t x) {
@@ -114,6 +126,9 @@ __device__ __forceinline__ double start_value(const PiArgs &a, int i, const T *c
 }
 
 // ------------------------------------------------------------------ partial sums
+// A = sum y (the mean must be removed to rounding level relative to |y|, so
+// it needs float-float like B = sum y^2 and C = sum y y_prev, which decide
+// the stopping cosine).
 struct Part {
     ff A, B, C;
 };
@@ -126,17 +141,33 @@ __device__ __forceinline__ Part part_zero() {
 
 __device__ __forceinline__ Part part_add(Part x, Part y) {
     Part r;
-    r.A = ff_add(x.A, y.A);
-    r.B = ff_add(x.B, y.B);
-    r.C = ff_add(x.C, y.C);
+    r.A = ff_add_lazy(x.A, y.A);
+    r.B = ff_add_lazy(x.B, y.B);
+    r.C = ff_add_lazy(x.C, y.C);
     return r;
 }
 
-__device__ __forceinline__ Part warp_sum_part(Part p) {
-    p.A = warp_sum_ff(p.A);
-    p.B = warp_sum_ff(p.B);
-    p.C = warp_sum_ff(p.C);
+// Sum over lanes 0, lo, 2 lo, ... (lo a power of two; lanes between hold
+// nothing), taking the xor tree from stride 16 down to lo in a fixed order.
+// The sum ends in lane 0 (and every lane of its residue class), renormalised.
+__device__ __forceinline__ Part warp_sum_part(Part p, int lo = 1, int width = 32) {
+    for (int o = width >> 1; o >= lo; o >>= 1) {
+        Part q;
+        q.A = shfl_xor_ff(p.A, o);
+        q.B = shfl_xor_ff(p.B, o);
+        q.C = shfl_xor_ff(p.C, o);
+        p = part_add(p, q);
+    }
+    p.A = ff_norm(p.A);
+    p.B = ff_norm(p.B);
+    p.C = ff_norm(p.C);
     return p;
+}
+
+__device__ __forceinline__ int pow2_at_least(int v) {
+    int w = 1;
+    while (w < v) w <<= 1;
+    return w;
 }
 
 // Per-thread accumulation of (sum y, sum y^2, sum y x) for one sweep.
@@ -148,15 +179,15 @@ struct Acc<float> {
     ff A, B, C;
     __device__ __forceinline__ void reset() { A = B = C = ff_zero(); }
     __device__ __forceinline__ void add(float y, float x) {
-        A = ff_add_f(A, y);
-        B = ff_add(B, two_prod(y, y));
-        C = ff_add(C, two_prod(y, x));
+        A = ff_add_lazy(A, ff_make(y, 0.f));
+        B = ff_add_lazy(B, two_prod(y, y));
+        C = ff_add_lazy(C, two_prod(y, x));
     }
     __device__ __forceinline__ Part get() const {
         Part p;
-        p.A = A;
-        p.B = B;
-        p.C = C;
+        p.A = ff_norm(A);
+        p.B = ff_norm(B);
+        p.C = ff_norm(C);
         return p;
     }
 };
@@ -221,11 +252,13 @@ __device__ __forceinline__ double to_d(ff a) { return ff_to_double(a); }
 __device__ __forceinline__ void ctrl_step(const PiArgs &a, int s, const Part &P, Ctl &c,
                                           Slot *next, bool count_exit) {
     const float nf = (float)a.n;
+    // the mean is at rounding level: n mu^2 and n mu mu_prev need no extra
+    // precision, mu itself does (it is subtracted from the iterate)
     const ff mu = ff_mul(P.A, c.inv_n);
-    const ff ss = ff_sub(P.B, ff_mul_f(ff_mul(mu, mu), nf));
-    const ff cs = ff_sub(P.C, ff_mul_f(ff_mul(mu, c.mu_prev), nf));
+    const ff ss = ff_add_f(P.B, -nf * mu.hi * mu.hi);
+    const ff cs = ff_add_f(P.C, -nf * mu.hi * c.mu_prev.hi);
     // annihilated: ||proj y_s|| <= 64 eps 2^{e_{s-1}} ||proj y_{s-1}||
-    const bool zero = ss.hi <= kZeroTol2f * ldexpf(c.ss_prev.hi, 2 * c.e_prev);
+    const bool zero = ss.hi <= a.zero_tol2 * ldexpf(c.ss_prev.hi, 2 * c.e_prev);
     // cos_s >= 1 - tol  <=>  cs > 0 and cs^2 >= (1 - tol)^2 ss_s ss_{s-1}
     const bool conv = cs.hi > 0.f && !ff_lt(ff_mul(cs, cs), ff_mul(ff_mul(ss, c.ss_prev), c.omt2));
     bool stop = zero;
@@ -378,8 +411,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
             cmu = a.cres->mu;
             cinv = a.cres->inv_s;
         }
-        Acc<float> acc;   // start sums in float-float (A, B)
-        acc.reset();
+        // start sums: A = sum y_0 (not small after a prolongation), B = sum y_0^2
+        Part acc = part_zero();
         for (int i = r0 + tid; i < r1; i += blockDim.x) {
             const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
             ring0[i] = xt;
@@ -392,7 +425,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
             acc.A = ff_add(acc.A, v);
             acc.B = ff_add(acc.B, ff_mul(v, v));
         }
-        Part p = warp_sum_part(acc.get());
+        Part p = warp_sum_part(acc);
         if (lane == 0) s_pw[warp] = p;
         __syncthreads();
         if (warp == 0) {
@@ -600,10 +633,15 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
 }
 
 // ================================================================== small kernel
-// Shared memory: ring[3][n] T, gd[n] (FP64), w[m] T, rp[n+1] int, col[m] int.
+// Shared memory: ring[3][n] T, gd[n] (FP64 form), w[E] T, rp[n+1] int,
+// col[E] int, slice offsets[n/32 + 2] int.  E = nnz (CSR) or the SELL-32
+// size (one lane per row: each 32-row slice stores entry k of its rows
+// contiguously, rows padded to the slice's longest with zero weights, so the
+// lanes of a warp read consecutive words -- no bank conflicts).
 template <typename T>
-constexpr size_t small_smem_bytes(long long n, long long m) {
-    return (size_t)(sizeof(T) * (3 * n + m) + (sizeof(T) == 8 ? 8 * n : 0) + 4 * (n + 1) + 4 * m + 64);
+constexpr size_t small_smem_bytes(long long n, long long e) {
+    return (size_t)(sizeof(T) * (3 * n + e) + (sizeof(T) == 8 ? 8 * n : 0) + 4 * (n + 1) + 4 * e +
+                    4 * (n / 32 + 2) + 64);
 }
 
 template <typename T, int G>
@@ -611,12 +649,15 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int n = a.n;
     const int m = a.rp[n];
+    const bool sell = (G == 1) && a.sell_nnz > 0;
+    const int E = sell ? (int)a.sell_nnz : m;
     const bool fp64 = sizeof(T) == 8;
     T *ring0 = reinterpret_cast<T *>(smem_raw);
     double *s_gd = reinterpret_cast<double *>(ring0 + 3 * n);
     T *s_w = fp64 ? reinterpret_cast<T *>(s_gd + n) : ring0 + 3 * n;
-    int *s_rp = reinterpret_cast<int *>(s_w + m);
+    int *s_rp = reinterpret_cast<int *>(s_w + E);
     int *s_col = s_rp + n + 1;
+    int *s_soff = s_col + E;
     __shared__ Part s_pw[2][32];
     __shared__ Slot s_slot[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -627,9 +668,40 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     const double inv_gd = 1.0 / a.g;
 
     for (int i = tid; i <= n; i += blockDim.x) s_rp[i] = a.rp[i];
-    for (int e = tid; e < m; e += blockDim.x) {
-        s_col[e] = a.col[e];
-        s_w[e] = wv[e];
+    const int nsl = (n + 31) / 32;
+    if (sell) {
+        for (int q = tid; q < nsl; q += blockDim.x) {
+            int L = 0;
+            for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, a.rp[r + 1] - a.rp[r]);
+            s_soff[q + 1] = 32 * L;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            s_soff[0] = 0;
+            for (int q = 0; q < nsl; q++) s_soff[q + 1] += s_soff[q];
+        }
+        __syncthreads();
+        for (int i = tid; i < 32 * nsl; i += blockDim.x) {
+            const int q = i >> 5, l = i & 31;
+            const int L = (s_soff[q + 1] - s_soff[q]) >> 5;
+            const int e0 = (i < n) ? a.rp[i] : 0;
+            const int len = (i < n) ? a.rp[i + 1] - e0 : 0;
+            for (int k = 0; k < L; k++) {
+                const int idx = s_soff[q] + 32 * k + l;
+                if (k < len) {
+                    s_col[idx] = a.col[e0 + k];
+                    s_w[idx] = wv[e0 + k];
+                } else {
+                    s_col[idx] = (i < n) ? i : 0;   // zero weight: no contribution
+                    s_w[idx] = (T)0;
+                }
+            }
+        }
+    } else {
+        for (int e = tid; e < m; e += blockDim.x) {
+            s_col[e] = a.col[e];
+            s_w[e] = wv[e];
+        }
     }
     {
         const T *cb = nullptr;
@@ -639,8 +711,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
             cmu = a.cres->mu;
             cinv = a.cres->inv_s;
         }
-        Acc<float> acc;
-        acc.reset();
+        Part acc = part_zero();
         for (int i = tid; i < n; i += blockDim.x) {
             const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
             ring0[i] = xt;
@@ -653,7 +724,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
             acc.A = ff_add(acc.A, v);
             acc.B = ff_add(acc.B, ff_mul(v, v));
         }
-        Part p = warp_sum_part(acc.get());
+        Part p = warp_sum_part(acc);
         if (lane == 0) s_pw[0][warp] = p;
     }
     __syncthreads();
@@ -692,14 +763,17 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
         const T *x = ring0 + (size_t)(s % 3) * n;
         T *y = ring0 + (size_t)((s + 1) % 3) * n;
         if (warp == 0) {
+            if (lane == 0) TRACE(s, 0);
             if (s >= 1) {
                 Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
-                q = warp_sum_part(q);
+                q = warp_sum_part(q, 1, pow2_at_least(nw));
                 Slot nx;
                 ctrl_step(a, s, q, c, &nx, false);
                 if (lane == 0) s_slot[s & 1] = nx;
             }
+            if (lane == 0) TRACE(s, 1);
         } else {
+            if (lane == 0 && warp == 1) TRACE(s, 4);
             const T mT = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
             const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
             const T gm = g * mT;
@@ -709,17 +783,64 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
                 if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
                 const int i = base;
                 T ac = (T)0, xi = (T)0;
-                if (i < n) {
-                    xi = x[i];
-                    if (fp64) {
-                        for (int e = s_rp[i] + rlane, e1 = s_rp[i + 1]; e < e1; e += G)
-                            ac = fma(s_w[e], x[s_col[e]], ac);
-                    } else {
-                        for (int e = s_rp[i] + rlane, e1 = s_rp[i + 1]; e < e1; e += G)
-                            ac += s_w[e] * (xi - x[s_col[e]]);
+                if (sell) {
+                    // one lane per row, 32 rows per warp = one slice; padded
+                    // entries have zero weight
+                    const int q = base >> 5;
+                    const int off = s_soff[q] + (base & 31);
+                    const int L = (s_soff[q + 1] - s_soff[q]) >> 5;
+                    xi = (i < n) ? x[i] : (T)0;
+                    T a0 = (T)0, a1 = (T)0;
+                    int k = 0;
+                    for (; k + 1 < L; k += 2) {
+                        const int c0 = s_col[off + 32 * k], c1 = s_col[off + 32 * k + 32];
+                        const T w0 = s_w[off + 32 * k], w1 = s_w[off + 32 * k + 32];
+                        const T x0 = x[c0], x1 = x[c1];
+                        if (fp64) {
+                            a0 = fma(w0, x0, a0);
+                            a1 = fma(w1, x1, a1);
+                        } else {
+                            a0 += w0 * (xi - x0);
+                            a1 += w1 * (xi - x1);
+                        }
                     }
+                    if (k < L) {
+                        const T w0 = s_w[off + 32 * k], x0 = x[s_col[off + 32 * k]];
+                        if (fp64) a0 = fma(w0, x0, a0);
+                        else a0 += w0 * (xi - x0);
+                    }
+                    ac = a0 + a1;
+                } else if (i < n) {
+                    xi = x[i];
+                    // four independent accumulators: the loads of four entries
+                    // are in flight together
+                    T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+                    int e = s_rp[i] + rlane;
+                    const int e1 = s_rp[i + 1];
+                    for (; e + 3 * G < e1; e += 4 * G) {
+                        const int c0 = s_col[e], c1 = s_col[e + G], c2 = s_col[e + 2 * G], c3 = s_col[e + 3 * G];
+                        const T w0 = s_w[e], w1 = s_w[e + G], w2 = s_w[e + 2 * G], w3 = s_w[e + 3 * G];
+                        const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
+                        if (fp64) {
+                            a0 = fma(w0, x0, a0);
+                            a1 = fma(w1, x1, a1);
+                            a2 = fma(w2, x2, a2);
+                            a3 = fma(w3, x3, a3);
+                        } else {
+                            a0 += w0 * (xi - x0);
+                            a1 += w1 * (xi - x1);
+                            a2 += w2 * (xi - x2);
+                            a3 += w3 * (xi - x3);
+                        }
+                    }
+                    for (; e < e1; e += G) {
+                        if (fp64) a0 = fma(s_w[e], x[s_col[e]], a0);
+                        else a0 += s_w[e] * (xi - x[s_col[e]]);
+                    }
+                    ac = (a0 + a1) + (a2 + a3);
                 }
                 ac = group_sum<G>(ac);
+                if (lane == 0 && warp == 1) TRACE(s, 5);
                 if (i < n && rlane == 0) {
                     T yv;
                     if (fp64) yv = (T)((fma(s_gd[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
@@ -727,9 +848,13 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
                     y[i] = yv;
                     acc.add(yv, xi);
                 }
+                if (lane == 0 && warp == 1) TRACE(s, 6);
             }
-            Part p = warp_sum_part(acc.get());
+            // only the lanes leading a row group hold sums
+            Part p = warp_sum_part(acc.get(), G);
             if (lane == 0) s_pw[(s + 1) & 1][warp] = p;
+            if (lane == 0 && warp == 1) TRACE(s, 2);
+            if (lane == 0 && warp == nw - 1) TRACE(s, 3);
         }
         __syncthreads();
         s++;
@@ -738,7 +863,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     if (warp == 0) {
         if (exit_kind == 2 && !no_sweeps) {
             Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
-            q = warp_sum_part(q);
+            q = warp_sum_part(q, 1, pow2_at_least(nw));
             ctrl_step(a, s, q, c, nullptr, true);
         }
         if (lane == 0) {
@@ -808,13 +933,14 @@ static int small_lanes(int n, long long nnz, int fp32) {
     const double avg = (double)nnz / (double)std::max(1, n);
     int g = 1;
     if (fp32) {
-        // a row per lane while rows are short: every extra lane costs a share
-        // of the per-sweep float-float reduction
-        while (g < 32 && g * 24 < avg) g <<= 1;
+        // a row per lane while a lane's (unrolled) entry loop stays short:
+        // every lane that holds a row pays its share of the per-sweep
+        // float-float reduction
+        while (g < 32 && g * 32 < avg) g <<= 1;
     } else {
         // FP64: every lane-operation costs FP64 issue slots, so use the fewest
-        // lanes that keep each lane's dependent FMA chain to about 8 entries
-        while (g < 32 && g * 8 < avg) g <<= 1;
+        // lanes that keep each lane's dependent FMA chain short
+        while (g < 32 && g * 16 < avg) g <<= 1;
     }
     return g;
 }
@@ -827,11 +953,43 @@ static int small_threads(int n, int G) {
     return 32 * (w + 1);
 }
 
-bool small_level_fits(int n, long long nnz, int fp32) {
+// Entries the small kernel stores: the SELL-32 size with one lane per row
+// (when known), else the CSR size.
+static long long small_entries(const PiLevel &lv, int G) {
+    return (G == 1 && lv.sell_nnz > 0) ? lv.sell_nnz : lv.nnz;
+}
+
+static size_t small_bytes(const PiLevel &lv, int G, int fp32) {
+    const long long e = small_entries(lv, G);
+    return fp32 ? small_smem_bytes<float>(lv.n, e) : small_smem_bytes<double>(lv.n, e);
+}
+
+bool small_level_fits(const PiLevel &lv, int fp32) {
     DeviceInfo d;
     if (device_info(&d) != CMG_OK) return false;
-    const size_t b = fp32 ? small_smem_bytes<float>(n, nnz) : small_smem_bytes<double>(n, nnz);
-    return b + 4096 <= (size_t)d.max_smem_optin;
+    const int G = small_lanes(lv.n, lv.nnz, fp32);
+    return small_bytes(lv, G, fp32) + 4096 <= (size_t)d.max_smem_optin;
+}
+
+__global__ void k_sell_size(int n, const int *__restrict__ rp, unsigned long long *out) {
+    const int nsl = (n + 31) / 32;
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsl; q += gridDim.x * blockDim.x) {
+        int L = 0;
+        for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, rp[r + 1] - rp[r]);
+        atomicAdd(out, (unsigned long long)(32 * L));
+    }
+}
+
+cmg_status_t sell_size(int n, const int *rp, unsigned long long *dev_counter, long long *out,
+                       cudaStream_t s) {
+    CMG_CUDA(cudaMemsetAsync(dev_counter, 0, sizeof(unsigned long long), s));
+    k_sell_size<<<grid_for((n + 31) / 32, 256), 256, 0, s>>>(n, rp, dev_counter);
+    CMG_TRY(launch_status());
+    unsigned long long v = 0;
+    CMG_CUDA(cudaMemcpyAsync(&v, dev_counter, sizeof(v), cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaStreamSynchronize(s));
+    *out = (long long)v;
+    return CMG_OK;
 }
 
 cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
@@ -862,12 +1020,13 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.gd = run.gd;
     a.res = run.res;
     a.partials = nullptr;
+    a.zero_tol2 = run.fp32 ? kZeroTol2_32 : kZeroTol2_64;
+    a.sell_nnz = lv.sell_nnz;
     void *args[] = {&a, &gs};
-    if (small_level_fits(lv.n, lv.nnz, run.fp32)) {
+    if (small_level_fits(lv, run.fp32)) {
         const int G = small_lanes(lv.n, lv.nnz, run.fp32);
         const void *kern = run.fp32 ? small_kernel<float>(G) : small_kernel<double>(G);
-        const size_t smem = run.fp32 ? small_smem_bytes<float>(lv.n, lv.nnz)
-                                     : small_smem_bytes<double>(lv.n, lv.nnz);
+        const size_t smem = small_bytes(lv, G, run.fp32);
         CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         return coop_launch(kern, 1, small_threads(lv.n, G), smem, s, args, gs);
     }
@@ -1210,3 +1369,9 @@ cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const Pi
 }
 
 }  // namespace cmg
+
+#ifdef CMG_TRACE
+extern "C" int cmg_debug_trace(long long *out) {
+    return (int)cudaMemcpyFromSymbol(out, cmg::g_trace, sizeof(cmg::g_trace));
+}
+#endif
