@@ -198,8 +198,10 @@ def run_gpu(args):
         opts = cmg.options(seed=1412, timing=1, precision=precision)
         u = torch.empty(n, dtype=torch.float64, device="cuda")
 
-        def step():
+        def step(mid=None):
             h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
+            if mid is not None:
+                mid.record(stream)
             _, lam, st = h.fiedler(u_out=u, stream=sid)
             h.close()
             return lam, st
@@ -208,16 +210,18 @@ def run_gpu(args):
             step()
         barrier()
         l0 = cmg.kernel_launches()
-        step_ms, stats = [], []
+        step_ms, setup_ms, stats = [], [], []
         for _ in range(steps):
             flush.zero_()
             e0 = torch.cuda.Event(enable_timing=True)
+            em = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            lam, st = step()
+            lam, st = step(em)
             e1.record(stream)
             e1.synchronize()
             step_ms.append(e0.elapsed_time(e1))
+            setup_ms.append(e0.elapsed_time(em))
             stats.append(st)
         barrier()
         launches = cmg.kernel_launches() - l0
@@ -229,6 +233,8 @@ def run_gpu(args):
         srt = sorted(step_ms)
         return {"value": world * steps / (total / 1e3), "ms_per_step": total / steps,
                 "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
+                "setup_ms": statistics.median(setup_ms),
+                "solve_ms": statistics.median(a - b for a, b in zip(step_ms, setup_ms)),
                 "stats": stats, "launches": launches, "u": u.cpu().numpy(), "lam": lam}
 
     with ClockSampler(local) as clk:
@@ -320,11 +326,13 @@ def run_gpu(args):
                            l2="256 MB buffer written between timed steps (flush)",
                            parallelism=f"replicas{world}"),
             "latency_ms": {"p50": r32["p50_ms"], "p99": r32["p99_ms"]},
+            "split_ms": {"setup": r32["setup_ms"], "solve": r32["solve_ms"]},
             "levels": {"n": st32["n"], "nnz": st32["nnz"], "sweeps": st32["sweeps"],
                        "level_ms": [round(x, 4) for x in st32["level_ms"]]},
             "lambda2": st32["lambda2"], "residual": st32["residual"],
             "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
                      "latency_ms": {"p50": r64["p50_ms"], "p99": r64["p99_ms"]},
+                     "split_ms": {"setup": r64["setup_ms"], "solve": r64["solve_ms"]},
                      "sweeps": st64["sweeps"], "level_ms": [round(x, 4) for x in st64["level_ms"]],
                      "lambda2": st64["lambda2"], "residual": st64["residual"],
                      "level0_launch": {"ms": ms0_64, "bytes": by0_64,

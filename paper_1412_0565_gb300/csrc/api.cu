@@ -216,39 +216,71 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         CMG_CUDA(cudaMemcpyAsync(&Z.g, gd, sizeof(double), cudaMemcpyDeviceToHost, s));
         CMG_CUDA(cudaStreamSynchronize(s));
     }
-    // ---- Alg. 1 Step 1: coarsen while n_i > coarse_size
+    // ---- Alg. 1 Step 1: coarsen while n_i > coarse_size.  Each level runs
+    // HEC, the Galerkin product and the SELL-32 sizing on the device into
+    // buffers sized by upper bounds, then reads its sizes back with one
+    // host synchronisation and moves the coarse CSR into exact allocations.
+    LevelCounts *cnt_dev;
+    CMG_TRY(scr.get(&cnt_dev, 1));
     int level = 0;
     while (h->lv.back().n > o.coarse_size && (int)h->lv.size() < o.max_levels) {
-        LevelData &F = h->lv.back();
-        int *agg = nullptr;
-        CMG_TRY(dev_alloc_n(&agg, (size_t)F.n, s));
-        int c = 0;
-        cmg_status_t st = hec_level(F.n, F.nnz, F.rp, F.col, F.w, o.seed, level, nullptr, agg, &c, s);
-        if (st != CMG_OK) {
+        const LevelData F = h->lv.back();
+        int *agg = nullptr, *rp_t = nullptr, *col_t = nullptr;
+        double *w_t = nullptr;
+        LevelCounts hc;
+        auto release = [&]() {
             dev_free(agg, s);
-            return st;
-        }
-        if (c < 2) {  // HEC collapsed the level: it becomes the coarsest
-            dev_free(agg, s);
+            dev_free(rp_t, s);
+            dev_free(col_t, s);
+            dev_free(w_t, s);
+        };
+        cmg_status_t st = CMG_OK;
+        do {
+            const size_t cap = (size_t)std::max<long long>(F.nnz, 1);
+            if ((st = dev_alloc_n(&agg, (size_t)F.n, s)) != CMG_OK) break;
+            if ((st = dev_alloc_n(&rp_t, (size_t)F.n + 1, s)) != CMG_OK) break;
+            if ((st = dev_alloc_n(&col_t, cap, s)) != CMG_OK) break;
+            if ((st = dev_alloc_n(&w_t, cap, s)) != CMG_OK) break;
+            if ((st = from_cuda(cudaMemsetAsync(cnt_dev, 0, sizeof(LevelCounts), s))) != CMG_OK) break;
+            st = hec_level_async(F.n, F.nnz, F.rp, F.col, F.w, o.seed, level, nullptr, agg,
+                                 &cnt_dev->c, &cnt_dev->gs, s);
+            if (st != CMG_OK) break;
+            st = galerkin_async(F.n, F.nnz, F.rp, F.col, F.w, agg, bits_for(F.n), cnt_dev, rp_t,
+                                col_t, w_t, s);
+            if (st != CMG_OK) break;
+            if ((st = sell_size_async(&cnt_dev->c, F.n, rp_t, &cnt_dev->sell, s)) != CMG_OK) break;
+            st = from_cuda(cudaMemcpyAsync(&hc, cnt_dev, sizeof(hc), cudaMemcpyDeviceToHost, s));
+            if (st != CMG_OK) break;
+            if ((st = from_cuda(cudaStreamSynchronize(s))) != CMG_OK) break;
+            if (hc.gs.err) st = CMG_ERR_DEVICE_TIMEOUT;
+        } while (0);
+        if (st != CMG_OK || hc.c < 2) {  // c < 2: HEC collapsed the level, it is the coarsest
+            release();
+            if (st != CMG_OK) return st;
             break;
         }
-        F.agg = agg;
-        CoarseCSR cc = {};
-        st = galerkin(F.n, F.nnz, F.rp, F.col, F.w, agg, c, &cc, s);
-        if (st != CMG_OK) {
-            dev_free(cc.rp, s);
-            dev_free(cc.col, s);
-            dev_free(cc.w, s);
-            return st;
-        }
         LevelData C;
-        C.n = cc.n;
-        C.nnz = cc.nnz;
-        C.rp = cc.rp;
-        C.col = cc.col;
-        C.w = cc.w;
-        C.g = cc.g;
-        h->lv.push_back(C);
+        C.n = hc.c;
+        C.nnz = hc.nseg;
+        memcpy(&C.g, &hc.gbits, sizeof(double));
+        C.sell_nnz = (C.n <= 65536) ? (long long)hc.sell : 0;
+        st = dev_alloc_n(&C.rp, (size_t)C.n + 1, s);
+        if (st == CMG_OK) st = dev_alloc_n(&C.col, (size_t)std::max<long long>(C.nnz, 1), s);
+        if (st == CMG_OK) st = dev_alloc_n(&C.w, (size_t)std::max<long long>(C.nnz, 1), s);
+        if (st == CMG_OK)
+            st = from_cuda(cudaMemcpyAsync(C.rp, rp_t, sizeof(int) * ((size_t)C.n + 1),
+                                           cudaMemcpyDeviceToDevice, s));
+        if (st == CMG_OK && C.nnz > 0)
+            st = from_cuda(cudaMemcpyAsync(C.col, col_t, sizeof(int) * (size_t)C.nnz,
+                                           cudaMemcpyDeviceToDevice, s));
+        if (st == CMG_OK && C.nnz > 0)
+            st = from_cuda(cudaMemcpyAsync(C.w, w_t, sizeof(double) * (size_t)C.nnz,
+                                           cudaMemcpyDeviceToDevice, s));
+        h->lv.back().agg = agg;
+        agg = nullptr;
+        release();
+        h->lv.push_back(C);  // freed with the hierarchy, also on error
+        if (st != CMG_OK) return st;
         level++;
     }
     // ---- FP32 copies of the weights for the FP32 sweep form
@@ -269,7 +301,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
             L.ntiles = tile_count(L.n, L.nnz);
             CMG_TRY(dev_alloc_n(&L.tiles, (size_t)L.ntiles + 1, s));
             CMG_TRY(build_tiles(L.n, L.nnz, L.rp, L.tiles, s));
-            if (L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
+            if (&L == &h->lv.front() && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
         }
     }
     // ---- solve workspace: a buffer pair per level, results, barrier state

@@ -19,11 +19,10 @@
 
 namespace cmg {
 
-static int bits_for(int c) {
-    int b = 1;
-    while ((1ll << b) < (long long)c) b++;
-    return b;
-}
+// Every kernel below reads the sizes it depends on (aggregate count c,
+// cross-entry count, coarse nnz) from device memory, so the product runs
+// without host synchronisation; grids are sized by upper bounds (c <= n,
+// records <= nnz).
 
 __global__ void k_count_cross(int n, const int *__restrict__ rp, const int *__restrict__ col,
                               const int *__restrict__ agg, int *__restrict__ cnt) {
@@ -35,9 +34,14 @@ __global__ void k_count_cross(int n, const int *__restrict__ rp, const int *__re
     }
 }
 
+// off[n] holds the cross-entry count; records (a, b) go to [0, ncross),
+// records (b, a) to [ncross, 2 ncross).
 __global__ void k_emit(int n, const int *__restrict__ rp, const int *__restrict__ col,
                        const int *__restrict__ agg, const int *__restrict__ off, int bb,
-                       long long ncross, uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+                       uint64_t *__restrict__ keys, uint32_t *__restrict__ vals,
+                       LevelCounts *__restrict__ cnt) {
+    const long long ncross = off[n];
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt->m = (int)(2 * ncross);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const uint64_t a = (uint64_t)agg[i];
         long long k = off[i];
@@ -54,18 +58,22 @@ __global__ void k_emit(int n, const int *__restrict__ rp, const int *__restrict_
     }
 }
 
-__global__ void k_heads(long long m, const uint64_t *__restrict__ keys, int *__restrict__ head) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
+// head[k] = 1 where a group of equal keys starts, 0 elsewhere (and past m).
+__global__ void k_heads(long long cap, const uint64_t *__restrict__ keys,
+                        const LevelCounts *__restrict__ cnt, int *__restrict__ head) {
+    const long long m = cnt->m;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < cap;
          k += (long long)gridDim.x * blockDim.x)
-        head[k] = (k == 0 || keys[k] != keys[k - 1]) ? 1 : 0;
+        head[k] = (k < m && (k == 0 || keys[k] != keys[k - 1])) ? 1 : 0;
 }
 
 // One thread per segment (group of equal keys): left-to-right FP64 sum.
-__global__ void k_segsum(long long m, const uint64_t *__restrict__ keys,
+__global__ void k_segsum(long long cap, const uint64_t *__restrict__ keys,
                          const uint32_t *__restrict__ vals, const int *__restrict__ head,
                          const int *__restrict__ segid, const double *__restrict__ w, int bb,
-                         int *__restrict__ col_c, double *__restrict__ w_c,
-                         int *__restrict__ row_of) {
+                         const LevelCounts *__restrict__ cnt, int *__restrict__ col_c,
+                         double *__restrict__ w_c, int *__restrict__ row_of) {
+    const long long m = cnt->m;
     const uint64_t mask = (1ull << bb) - 1ull;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m;
          k += (long long)gridDim.x * blockDim.x) {
@@ -84,8 +92,14 @@ __global__ void k_segsum(long long m, const uint64_t *__restrict__ keys,
     }
 }
 
-// Coarse row pointers from the (row-sorted) segment rows.
-__global__ void k_rowptr(int nseg, int c, const int *__restrict__ row_of, int *__restrict__ rp_c) {
+// Coarse row pointers from the (row-sorted) segment rows; segid[cap] holds
+// the segment count, which is also recorded as the coarse nnz.
+__global__ void k_rowptr(long long cap, const int *__restrict__ segid,
+                         const int *__restrict__ row_of, LevelCounts *__restrict__ cnt,
+                         int *__restrict__ rp_c) {
+    const int nseg = segid[cap];
+    const int c = cnt->c;
+    if (blockIdx.x == 0 && threadIdx.x == 0) cnt->nseg = nseg;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= nseg; s += gridDim.x * blockDim.x) {
         const int lo = (s == 0) ? -1 : row_of[s - 1];
         const int hi = (s == nseg) ? c : row_of[s];
@@ -94,8 +108,10 @@ __global__ void k_rowptr(int nseg, int c, const int *__restrict__ row_of, int *_
 }
 
 // g = max_i (d_i + d_i), d_i = sum_j w_ij left to right (Alg. 3, first line).
-__global__ void k_gershgorin(int n, const int *__restrict__ rp, const double *__restrict__ w,
-                             unsigned long long *__restrict__ gbits) {
+// The row count is n_dev[0] when n_dev is given, else n.
+__global__ void k_gershgorin(int n, const int *__restrict__ n_dev, const int *__restrict__ rp,
+                             const double *__restrict__ w, unsigned long long *__restrict__ gbits) {
+    if (n_dev) n = *n_dev;
     double best = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double d = 0.0;
@@ -113,77 +129,48 @@ cmg_status_t launch_gershgorin(int n, const int *rp, const double *w, double *g_
     CMG_CUDA(cudaMemsetAsync(g_dev, 0, sizeof(double), s));
     const int threads = 256;
     k_gershgorin<<<grid_for(n, threads, 4), threads, 0, s>>>(
-        n, rp, w, reinterpret_cast<unsigned long long *>(g_dev));
+        n, nullptr, rp, w, reinterpret_cast<unsigned long long *>(g_dev));
     return launch_status();
 }
 
-cmg_status_t galerkin(int n, long long nnz, const int *rp, const int *col, const double *w,
-                      const int *agg, int c, CoarseCSR *out, cudaStream_t s) {
+cmg_status_t galerkin_async(int n, long long nnz, const int *rp, const int *col, const double *w,
+                            const int *agg, int key_bits, LevelCounts *cnt, int *rp_c, int *col_c,
+                            double *w_c, cudaStream_t s) {
     Scratch scr(s);
     const int threads = 256;
-    int *cnt, *off;
-    CMG_TRY(scr.get(&cnt, n));
+    // every cross pair {i, j} is stored twice in a symmetric CSR and counted
+    // once (agg(i) < agg(j)), so the record count 2 ncross is at most nnz
+    const long long cap = std::max<long long>(nnz, 1);
+    int *ccount, *off;
+    CMG_TRY(scr.get(&ccount, n));
     CMG_TRY(scr.get(&off, (size_t)n + 1));
-    k_count_cross<<<grid_for(n, threads), threads, 0, s>>>(n, rp, col, agg, cnt);
+    k_count_cross<<<grid_for(n, threads), threads, 0, s>>>(n, rp, col, agg, ccount);
     CMG_TRY(launch_status());
-    CMG_TRY(exclusive_scan(cnt, off, n, scr, s));
-    int ncross_i = 0;
-    CMG_CUDA(cudaMemcpyAsync(&ncross_i, off + n, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaStreamSynchronize(s));
-    const long long ncross = ncross_i;
-    const long long m = 2 * ncross;
-    const int bb = bits_for(c);
-
-    out->n = c;
-    out->rp = nullptr;
-    out->col = nullptr;
-    out->w = nullptr;
-    CMG_TRY(dev_alloc_n(&out->rp, (size_t)c + 1, s));
-    if (m == 0) {
-        CMG_CUDA(cudaMemsetAsync(out->rp, 0, sizeof(int) * ((size_t)c + 1), s));
-        out->nnz = 0;
-        CMG_TRY(dev_alloc_n(&out->col, 1, s));
-        CMG_TRY(dev_alloc_n(&out->w, 1, s));
-        double *gd;
-        CMG_TRY(scr.get(&gd, 1));
-        CMG_CUDA(cudaMemsetAsync(gd, 0, sizeof(double), s));
-        out->g = 0.0;
-        return CMG_OK;
-    }
+    CMG_TRY(exclusive_scan(ccount, off, n, scr, s));
     uint64_t *ka, *kb;
     uint32_t *va, *vb;
-    CMG_TRY(scr.get(&ka, (size_t)m));
-    CMG_TRY(scr.get(&kb, (size_t)m));
-    CMG_TRY(scr.get(&va, (size_t)m));
-    CMG_TRY(scr.get(&vb, (size_t)m));
-    k_emit<<<grid_for(n, threads), threads, 0, s>>>(n, rp, col, agg, off, bb, ncross, ka, va);
+    CMG_TRY(scr.get(&ka, (size_t)cap));
+    CMG_TRY(scr.get(&kb, (size_t)cap));
+    CMG_TRY(scr.get(&va, (size_t)cap));
+    CMG_TRY(scr.get(&vb, (size_t)cap));
+    k_emit<<<grid_for(n, threads), threads, 0, s>>>(n, rp, col, agg, off, key_bits, ka, va, cnt);
     CMG_TRY(launch_status());
-    CMG_TRY(radix_sort_pairs(&ka, &va, kb, vb, (int)m, 2 * bb, scr, s));
-
+    CMG_TRY(radix_sort_pairs(&ka, &va, kb, vb, (int)cap, &cnt->m, 2 * key_bits, scr, s));
     int *head, *segid, *row_of;
-    CMG_TRY(scr.get(&head, (size_t)m));
-    CMG_TRY(scr.get(&segid, (size_t)m + 1));
-    k_heads<<<grid_for(m, threads), threads, 0, s>>>(m, ka, head);
+    CMG_TRY(scr.get(&head, (size_t)cap));
+    CMG_TRY(scr.get(&segid, (size_t)cap + 1));
+    CMG_TRY(scr.get(&row_of, (size_t)cap));
+    k_heads<<<grid_for(cap, threads), threads, 0, s>>>(cap, ka, cnt, head);
     CMG_TRY(launch_status());
-    CMG_TRY(exclusive_scan(head, segid, (int)m, scr, s));
-    int nseg = 0;
-    CMG_CUDA(cudaMemcpyAsync(&nseg, segid + m, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaStreamSynchronize(s));
-    CMG_TRY(dev_alloc_n(&out->col, (size_t)nseg, s));
-    CMG_TRY(dev_alloc_n(&out->w, (size_t)nseg, s));
-    CMG_TRY(scr.get(&row_of, (size_t)nseg));
-    k_segsum<<<grid_for(m, threads), threads, 0, s>>>(m, ka, va, head, segid, w, bb, out->col,
-                                                      out->w, row_of);
+    CMG_TRY(exclusive_scan(head, segid, (int)cap, scr, s));
+    k_segsum<<<grid_for(cap, threads), threads, 0, s>>>(cap, ka, va, head, segid, w, key_bits, cnt,
+                                                        col_c, w_c, row_of);
     CMG_TRY(launch_status());
-    k_rowptr<<<grid_for((long long)nseg + 1, threads), threads, 0, s>>>(nseg, c, row_of, out->rp);
+    k_rowptr<<<grid_for(cap + 1, threads), threads, 0, s>>>(cap, segid, row_of, cnt, rp_c);
     CMG_TRY(launch_status());
-    out->nnz = nseg;
-    double *gd;
-    CMG_TRY(scr.get(&gd, 1));
-    CMG_TRY(launch_gershgorin(c, out->rp, out->w, gd, s));
-    CMG_CUDA(cudaMemcpyAsync(&out->g, gd, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaStreamSynchronize(s));
-    return CMG_OK;
+    CMG_CUDA(cudaMemsetAsync(&cnt->gbits, 0, sizeof(cnt->gbits), s));
+    k_gershgorin<<<grid_for(n, threads, 4), threads, 0, s>>>(n, &cnt->c, rp_c, w_c, &cnt->gbits);
+    return launch_status();
 }
 
 }  // namespace cmg

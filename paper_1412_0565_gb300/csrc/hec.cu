@@ -326,15 +326,14 @@ __global__ void k_hec_resolve(HecArgs a, GridSync *gs) {
     }
 }
 
-cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, const double *w,
-                       uint64_t seed, int level, const uint32_t *rank, int *agg_out, int *c_host,
-                       cudaStream_t s) {
+cmg_status_t hec_level_async(int n, long long nnz, const int *rp, const int *col, const double *w,
+                             uint64_t seed, int level, const uint32_t *rank, int *agg_out,
+                             int *c_dev, GridSync *gs, cudaStream_t s) {
     Scratch scr(s);
     int *m;
     uint32_t *r, *minA, *minU;
     unsigned char *state;
-    int *ids, *cta_tot, *undecided, *small;
-    GridSync *gs;
+    int *ids, *cta_tot, *undecided, *rounds;
     // every round decides at least the lowest-ranked undecided vertex
     const int max_rounds = n + 1;
     CMG_TRY(scr.get(&m, n));
@@ -343,8 +342,7 @@ cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, cons
     CMG_TRY(scr.get(&state, n));
     CMG_TRY(scr.get(&ids, n));
     CMG_TRY(scr.get(&undecided, 3));
-    CMG_TRY(scr.get(&small, 4));
-    CMG_TRY(scr.get(&gs, 1));
+    CMG_TRY(scr.get(&rounds, 1));
     if (!rank) {
         CMG_TRY(scr.get(&r, n));
         CMG_TRY(launch_ranks(n, seed, level, r, s));
@@ -373,17 +371,28 @@ cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, cons
     a.undecided = undecided;
     a.max_rounds = max_rounds;
     a.agg = agg_out;
-    a.c_out = small;
-    a.rounds_out = small + 1;
+    a.c_out = c_dev;
+    a.rounds_out = rounds;
     void *args[] = {&a, &gs};
-    CMG_TRY(coop_launch((const void *)k_hec_resolve, blocks, threads, 0, s, args, gs));
-    int host[2];
+    return coop_launch((const void *)k_hec_resolve, blocks, threads, 0, s, args, gs);
+}
+
+cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, const double *w,
+                       uint64_t seed, int level, const uint32_t *rank, int *agg_out, int *c_host,
+                       cudaStream_t s) {
+    Scratch scr(s);
+    int *c_dev;
+    GridSync *gs;
+    CMG_TRY(scr.get(&c_dev, 1));
+    CMG_TRY(scr.get(&gs, 1));
+    CMG_TRY(hec_level_async(n, nnz, rp, col, w, seed, level, rank, agg_out, c_dev, gs, s));
+    int c = 0;
     GridSync hgs;
-    CMG_CUDA(cudaMemcpyAsync(host, small, sizeof(int) * 2, cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaMemcpyAsync(&c, c_dev, sizeof(int), cudaMemcpyDeviceToHost, s));
     CMG_CUDA(cudaMemcpyAsync(&hgs, gs, sizeof(GridSync), cudaMemcpyDeviceToHost, s));
     CMG_CUDA(cudaStreamSynchronize(s));
     if (hgs.err) return CMG_ERR_DEVICE_TIMEOUT;
-    *c_host = host[0];
+    *c_host = c;
     return CMG_OK;
 }
 

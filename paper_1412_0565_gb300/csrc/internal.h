@@ -15,6 +15,10 @@ int lanes_for_avg(double avg);
 cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, const double *w,
                        uint64_t seed, int level, const uint32_t *rank, int *agg_out, int *c_host,
                        cudaStream_t s);
+// The same without host synchronisation: c to *c_dev, barrier state to *gs.
+cmg_status_t hec_level_async(int n, long long nnz, const int *rp, const int *col, const double *w,
+                             uint64_t seed, int level, const uint32_t *rank, int *agg_out,
+                             int *c_dev, GridSync *gs, cudaStream_t s);
 // avg = average row length (chooses the lanes per row).
 cmg_status_t launch_heaviest(int n, double avg, const int *rp, const int *col, const double *w,
                              int *m, cudaStream_t s);
@@ -23,25 +27,41 @@ cmg_status_t launch_ranks(int n, uint64_t seed, int level, uint32_t *r, cudaStre
 // ---------------------------------------------------------------- primitives.cu
 // Exclusive scan of int32 in[0..n) into out[0..n]; out[n] = total (device).
 cmg_status_t exclusive_scan(const int *in, int *out, int n, Scratch &scr, cudaStream_t s);
-// Stable LSD radix sort of (key, val) by the low `bits` bits of key.  On
-// return *keys / *vals point at the sorted arrays (one of the two buffers).
+// Stable LSD radix sort of (key, val) by the low `bits` bits of key; the item
+// count is read from device memory (count_dev) and is at most `cap`, the
+// buffers' capacity.  On return *keys / *vals point at the sorted arrays
+// (one of the two buffers).
 cmg_status_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
-                              uint32_t *vals_alt, int count, int bits, Scratch &scr,
-                              cudaStream_t s);
+                              uint32_t *vals_alt, int cap, const int *count_dev, int bits,
+                              Scratch &scr, cudaStream_t s);
 
 // ---------------------------------------------------------------- galerkin.cu
-struct CoarseCSR {
-    int n;
-    long long nnz;
-    int *rp;
-    int *col;
-    double *w;
-    double g;
+// Bits needed for the ids 0..c-1 (at least 1).
+inline int bits_for(int c) {
+    int b = 1;
+    while ((1ll << b) < (long long)c) b++;
+    return b;
+}
+
+// Device-side sizes of one coarsening step, read back once per level.
+struct LevelCounts {
+    int c;                      // aggregates (coarse vertices)
+    int m;                      // emitted Galerkin records (2 x cross entries)
+    int nseg;                   // coarse stored entries
+    int pad;
+    unsigned long long gbits;   // coarse Gershgorin shift (bits of a double)
+    unsigned long long sell;    // SELL-32 size of the coarse level
+    GridSync gs;                // barrier state of the coarsening kernel
 };
+
 // Galerkin product I L I^T of the level (rp, col, w) with aggregate map agg
-// onto c aggregates; allocates the coarse CSR (caller frees with dev_free).
-cmg_status_t galerkin(int n, long long nnz, const int *rp, const int *col, const double *w,
-                      const int *agg, int c, CoarseCSR *out, cudaStream_t s);
+// onto cnt->c aggregates (device), without host synchronisation.  Outputs
+// go to caller buffers sized by upper bounds: rp_c int[n+1], col_c int[nnz],
+// w_c double[nnz]; cnt->nseg and cnt->gbits receive the coarse nnz and g.
+// key_bits: bits of an upper bound of c (keys pack two aggregate ids).
+cmg_status_t galerkin_async(int n, long long nnz, const int *rp, const int *col, const double *w,
+                            const int *agg, int key_bits, LevelCounts *cnt, int *rp_c, int *col_c,
+                            double *w_c, cudaStream_t s);
 // Gershgorin shift g = max_i 2 * sum_j w_ij into *g_dev (device double).
 cmg_status_t launch_gershgorin(int n, const int *rp, const double *w, double *g_dev,
                                cudaStream_t s);
@@ -80,6 +100,10 @@ struct PiLevel {
 // dev_counter: one device unsigned long long of scratch.  Synchronises s.
 cmg_status_t sell_size(int n, const int *rp, unsigned long long *dev_counter, long long *out,
                        cudaStream_t s);
+// The same for a level whose row count is in device memory (at most n_cap),
+// without host synchronisation (the caller reads *dev_counter later).
+cmg_status_t sell_size_async(const int *n_dev, int n_cap, const int *rp,
+                             unsigned long long *dev_counter, cudaStream_t s);
 
 // Row tiles of a level for the tiled sweep kernel (tile_count + 1 entries).
 int tile_count(int n, long long nnz);

@@ -123,8 +123,10 @@ constexpr int kSortTile = kSortThreads * kSortRounds;
 constexpr int kSortWarps = kSortThreads / 32;
 
 // Per-tile digit histogram, stored digit-major: hist[d * ntiles + tile].
-__global__ void k_radix_hist(const uint64_t *__restrict__ keys, int count, int shift,
-                             int *__restrict__ hist) {
+// The item count is read from device memory (tiles past it count nothing).
+__global__ void k_radix_hist(const uint64_t *__restrict__ keys, const int *__restrict__ count_dev,
+                             int shift, int *__restrict__ hist) {
+    const int count = *count_dev;
     __shared__ int h[kRadix];
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) h[d] = 0;
     __syncthreads();
@@ -142,7 +144,9 @@ __global__ void k_radix_hist(const uint64_t *__restrict__ keys, int count, int s
 // which is their input order.
 __global__ void k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t *__restrict__ vin,
                                 uint64_t *__restrict__ kout, uint32_t *__restrict__ vout,
-                                int count, int shift, const int *__restrict__ offs) {
+                                const int *__restrict__ count_dev, int shift,
+                                const int *__restrict__ offs) {
+    const int count = *count_dev;
     __shared__ int running[kRadix];
     __shared__ int cnt[kSortWarps][kRadix];
     __shared__ int pre[kSortWarps][kRadix];
@@ -189,20 +193,20 @@ __global__ void k_radix_scatter(const uint64_t *__restrict__ kin, const uint32_t
 }
 
 cmg_status_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_alt,
-                              uint32_t *vals_alt, int count, int bits, Scratch &scr,
-                              cudaStream_t s) {
-    if (count <= 1 || bits <= 0) return CMG_OK;
-    const int ntiles = div_up(count, kSortTile);
+                              uint32_t *vals_alt, int cap, const int *count_dev, int bits,
+                              Scratch &scr, cudaStream_t s) {
+    if (cap <= 1 || bits <= 0) return CMG_OK;
+    const int ntiles = div_up(cap, kSortTile);
     int *hist, *offs;
     CMG_TRY(scr.get(&hist, (size_t)kRadix * ntiles));
     CMG_TRY(scr.get(&offs, (size_t)kRadix * ntiles + 1));
     uint64_t *ka = *keys, *kb = keys_alt;
     uint32_t *va = *vals, *vb = vals_alt;
     for (int shift = 0; shift < bits; shift += kRadixBits) {
-        k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, count, shift, hist);
+        k_radix_hist<<<ntiles, kSortThreads, 0, s>>>(ka, count_dev, shift, hist);
         CMG_TRY(launch_status());
         CMG_TRY(exclusive_scan(hist, offs, kRadix * ntiles, scr, s));
-        k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, count, shift, offs);
+        k_radix_scatter<<<ntiles, kSortThreads, 0, s>>>(ka, va, kb, vb, count_dev, shift, offs);
         CMG_TRY(launch_status());
         std::swap(ka, kb);
         std::swap(va, vb);

@@ -971,7 +971,9 @@ bool small_level_fits(const PiLevel &lv, int fp32) {
     return small_bytes(lv, G, fp32) + 4096 <= (size_t)d.max_smem_optin;
 }
 
-__global__ void k_sell_size(int n, const int *__restrict__ rp, unsigned long long *out) {
+__global__ void k_sell_size(int n_static, const int *__restrict__ n_dev, const int *__restrict__ rp,
+                            unsigned long long *out) {
+    const int n = n_dev ? *n_dev : n_static;
     const int nsl = (n + 31) / 32;
     for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nsl; q += gridDim.x * blockDim.x) {
         int L = 0;
@@ -983,13 +985,20 @@ __global__ void k_sell_size(int n, const int *__restrict__ rp, unsigned long lon
 cmg_status_t sell_size(int n, const int *rp, unsigned long long *dev_counter, long long *out,
                        cudaStream_t s) {
     CMG_CUDA(cudaMemsetAsync(dev_counter, 0, sizeof(unsigned long long), s));
-    k_sell_size<<<grid_for((n + 31) / 32, 256), 256, 0, s>>>(n, rp, dev_counter);
+    k_sell_size<<<grid_for((n + 31) / 32, 256), 256, 0, s>>>(n, nullptr, rp, dev_counter);
     CMG_TRY(launch_status());
     unsigned long long v = 0;
     CMG_CUDA(cudaMemcpyAsync(&v, dev_counter, sizeof(v), cudaMemcpyDeviceToHost, s));
     CMG_CUDA(cudaStreamSynchronize(s));
     *out = (long long)v;
     return CMG_OK;
+}
+
+cmg_status_t sell_size_async(const int *n_dev, int n_cap, const int *rp,
+                             unsigned long long *dev_counter, cudaStream_t s) {
+    CMG_CUDA(cudaMemsetAsync(dev_counter, 0, sizeof(unsigned long long), s));
+    k_sell_size<<<grid_for((n_cap + 31) / 32, 256), 256, 0, s>>>(n_cap, n_dev, rp, dev_counter);
+    return launch_status();
 }
 
 cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, const PiWorkspace *ws) {
