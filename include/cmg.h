@@ -172,6 +172,97 @@ cmg_status_t cmg_get_level_csr(cmg_hierarchy_t h, int32_t level, int64_t *row_pt
 cmg_status_t cmg_free(cmg_hierarchy_t h);
 
 /* ------------------------------------------------------------------------
+ * Batched form: many independent graphs set up and solved together.  The
+ * paper treats one graph; this form runs Alg. 1 on each graph of a batch
+ * with results equal to what cmg_setup / cmg_fiedler give for that graph
+ * alone (same hierarchy bit for bit, same vector within rounding), but with
+ * the whole batch in one block-diagonal union per level: one coarsening
+ * pass per level for all graphs, and one persistent kernel launch per level
+ * for the power iteration of every graph on that level, the launches
+ * replayed from a captured CUDA graph.
+ *
+ * Layout: graph q occupies rows graph_offsets[q] .. graph_offsets[q+1]-1 of
+ * one CSR (row_ptr int64[N+1], col int32[nnz], w double[nnz]) whose column
+ * indices are union indices; every entry of a row must stay inside the
+ * row's graph.  graph_offsets (host int64[G+1]) starts at 0, ends at N, and
+ * every graph has at least 2 vertices.  Result vectors use the same union
+ * layout.
+ * ---------------------------------------------------------------------- */
+typedef struct cmg_batch_s *cmg_batch_t;
+
+/* Batched Alg. 1 Step 1.  Same input contract per graph as cmg_setup (checked
+ * when opts->validate != 0; an entry leaving its graph is BAD_CSR).  A graph
+ * stops coarsening exactly where cmg_setup would stop it.
+ * Errors: as cmg_setup; INVALID_ARG also for num_graphs < 1 or offsets that
+ * are not non-decreasing; TOO_SMALL for a graph with fewer than 2 vertices. */
+cmg_status_t cmg_setup_batch(int32_t num_graphs, const int64_t *graph_offsets,
+                             const int64_t *row_ptr, const int32_t *col, const double *w,
+                             int32_t mem, const cmg_options_t *opts, void *stream,
+                             cmg_batch_t *out);
+
+/* Batched Alg. 1 Steps 2-3 for every graph of the batch.
+ *   u_out: double[N] in `u_mem` memory, or NULL: graph q's unit Fiedler vector
+ *     (sign rule of cmg_fiedler) in rows graph_offsets[q] .. graph_offsets[q+1]-1.
+ *   lambda2_out, residual_out (host double[G], nullable): per graph.
+ *   status_out (host int32[G], nullable): CMG_OK or CMG_WARN_MAXITER per graph.
+ * Returns WARN_MAXITER if any graph hit a sweep cap, else OK, or an error
+ * (INVALID_ARG, OOM, CUDA).  Synchronises `stream`. */
+cmg_status_t cmg_fiedler_batch(cmg_batch_t b, double *u_out, int32_t u_mem, double *lambda2_out,
+                               double *residual_out, int32_t *status_out, void *stream);
+
+/* Number of graphs, union levels, and the union size of level `level`
+ * (nullable outputs; level < 0 skips the sizes). */
+cmg_status_t cmg_batch_info(cmg_batch_t b, int32_t *num_graphs, int32_t *union_levels,
+                            int32_t level, int64_t *n_level, int64_t *nnz_level);
+
+/* Per-graph report of the last cmg_fiedler_batch (sizes, sweeps, cosines,
+ * lambda2, residual, status; level_ms and finalize_ms are 0).  Before the
+ * first solve, only levels / n / nnz are filled. */
+cmg_status_t cmg_batch_stats(cmg_batch_t b, int32_t graph, cmg_stats_t *stats_out);
+
+/* Graph `graph`'s aggregate map of level `level` onto level+1 in the graph's
+ * own numbering (host int32[n_level of that graph]); as cmg_get_aggregates. */
+cmg_status_t cmg_batch_get_aggregates(cmg_batch_t b, int32_t graph, int32_t level,
+                                      int32_t *agg_out);
+
+/* Graph `graph`'s CSR of level `level` in its own numbering; as
+ * cmg_get_level_csr (row_ptr int64[n+1], col int32[nnz], w double[nnz],
+ * g_out the level's Gershgorin shift; all nullable). */
+cmg_status_t cmg_batch_get_level_csr(cmg_batch_t b, int32_t graph, int32_t level, int64_t *row_ptr,
+                                     int32_t *col, double *w, double *g_out);
+
+/* Schedule REPLAY for a batch: exact sweep counts per graph and level, host
+ * int32[G * CMG_MAX_LEVELS] (graph-major); NULL returns to
+ * opts.replay_sweeps for every graph.  Used only when opts.schedule is
+ * CMG_SCHEDULE_REPLAY. */
+cmg_status_t cmg_batch_set_replay(cmg_batch_t b, const int32_t *sweeps);
+
+/* Launch shape of a union level's power-iteration kernel: `threads_per_graph`
+ * threads (32..1024, a multiple of 32) work on one graph at a time,
+ * `lanes_per_row` (1, 2, 4, 8, 16 or 32) of them on one row; a CTA holds
+ * `graphs_per_cta` such groups (tpg * gpc <= 1024; gpc <= 15 unless
+ * tpg = 32); `stage_csr` = 1 lets a group copy its graph's CSR into shared
+ * memory when it fits.  cmg_batch_config reads or sets one level's shape
+ * (set = 0 reads into the pointers, 1 writes them); cmg_batch_autotune times
+ * candidate shapes on the batch itself (a few sweeps per graph on every
+ * level, `stream`-ordered, synchronising) and keeps the fastest per level.
+ * Results do not depend on the shape beyond rounding. */
+typedef struct cmg_batch_shape {
+    int32_t threads_per_graph;
+    int32_t lanes_per_row;
+    int32_t graphs_per_cta;
+    int32_t stage_csr;
+} cmg_batch_shape_t;
+cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t set, cmg_batch_shape_t *shape);
+cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream);
+
+/* Device bytes held by the batch (levels and solve workspace). */
+cmg_status_t cmg_batch_device_bytes(cmg_batch_t b, size_t *bytes);
+
+/* Releases the batch. */
+cmg_status_t cmg_batch_free(cmg_batch_t b);
+
+/* ------------------------------------------------------------------------
  * Step entry points.  Each runs one step of the method on DEVICE buffers in
  * the library's internal layout (row_ptr as int32[n+1]) on `stream`; they
  * exist so every step can be checked on its own.  Inputs are assumed to meet

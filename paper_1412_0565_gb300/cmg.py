@@ -37,6 +37,9 @@ EXPORTS = [
     "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
     "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
     "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
+    "cmg_setup_batch", "cmg_fiedler_batch", "cmg_batch_info", "cmg_batch_stats",
+    "cmg_batch_get_aggregates", "cmg_batch_get_level_csr", "cmg_batch_set_replay",
+    "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_device_bytes", "cmg_batch_free",
 ]
 
 NOALLOC_MAX_N = 262144
@@ -78,6 +81,14 @@ class Stats(C.Structure):
                 "level_ms": list(self.level_ms[:L]), "finalize_ms": self.finalize_ms}
 
 
+class BatchShape(C.Structure):
+    _fields_ = [("threads_per_graph", C.c_int32), ("lanes_per_row", C.c_int32),
+                ("graphs_per_cta", C.c_int32), ("stage_csr", C.c_int32)]
+
+    def as_tuple(self):
+        return (self.threads_per_graph, self.lanes_per_row, self.graphs_per_cta, self.stage_csr)
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -115,6 +126,17 @@ def load(build_if_stale: bool = True):
             "cmg_power_sweeps_noalloc": (I32, [I32, V, V, V, F64, V, I32, V, P(F64), V]),
             "cmg_kernel_launches": (I32, [P(C.c_uint64)]),
             "cmg_debug_fail_alloc_after": (I32, [I64]),
+            "cmg_setup_batch": (I32, [I32, V, V, V, V, I32, P(Options), V, P(V)]),
+            "cmg_fiedler_batch": (I32, [V, V, I32, V, V, V, V]),
+            "cmg_batch_info": (I32, [V, P(I32), P(I32), I32, P(I64), P(I64)]),
+            "cmg_batch_stats": (I32, [V, I32, P(Stats)]),
+            "cmg_batch_get_aggregates": (I32, [V, I32, I32, V]),
+            "cmg_batch_get_level_csr": (I32, [V, I32, I32, V, V, V, P(F64)]),
+            "cmg_batch_set_replay": (I32, [V, V]),
+            "cmg_batch_config": (I32, [V, I32, I32, P(BatchShape)]),
+            "cmg_batch_autotune": (I32, [V, V]),
+            "cmg_batch_device_bytes": (I32, [V, P(C.c_size_t)]),
+            "cmg_batch_free": (I32, [V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -288,6 +310,127 @@ def fiedler(row_ptr, col, w, *, stream=None, **kw):
     """Alg. 1 end to end: setup + solve.  Returns (u, lambda2, stats)."""
     with Hierarchy(row_ptr, col, w, stream=stream, **kw) as h:
         return h.fiedler(stream=stream)
+
+
+class Batch:
+    """Batched Alg. 1 for many graphs: the union CSR (union column indices)
+    with vertex offsets `graph_offsets` (int64[G+1]).  `fiedler()` solves
+    every graph; results use the union layout."""
+
+    def __init__(self, graph_offsets, row_ptr, col, w, *, opts: Options | None = None,
+                 stream=None, **kw):
+        lib = load()
+        if opts is None:
+            opts = options(**kw)
+        self.opts = opts
+        offs = np.ascontiguousarray(graph_offsets, dtype=np.int64)
+        row_ptr, col, w = _as_inputs(row_ptr, col, w)
+        p_rp, mem = _ptr(row_ptr)
+        p_col, mem2 = _ptr(col)
+        p_w, mem3 = _ptr(w)
+        if not (mem == mem2 == mem3):
+            raise ValueError("row_ptr, col and w must all be host or all be device buffers")
+        self.G = len(offs) - 1
+        self.offsets = offs
+        self.N = int(offs[-1])
+        b = C.c_void_p()
+        self._b = None
+        st = lib.cmg_setup_batch(self.G, C.c_void_p(offs.ctypes.data), p_rp, p_col, p_w, mem,
+                                 C.byref(opts), _stream(stream), C.byref(b))
+        _check(st, "cmg_setup_batch", allow_warn=False)
+        self._b = b
+
+    def close(self):
+        if getattr(self, "_b", None):
+            load().cmg_batch_free(self._b)
+            self._b = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def union_levels(self) -> int:
+        L = C.c_int32()
+        _check(load().cmg_batch_info(self._b, None, C.byref(L), -1, None, None), "batch_info")
+        return L.value
+
+    def union_size(self, level: int):
+        n, nnz = C.c_int64(), C.c_int64()
+        _check(load().cmg_batch_info(self._b, None, None, level, C.byref(n), C.byref(nnz)), "info")
+        return n.value, nnz.value
+
+    def stats(self, graph: int) -> dict:
+        s = Stats()
+        _check(load().cmg_batch_stats(self._b, graph, C.byref(s)), "batch_stats")
+        return s.as_dict()
+
+    def aggregates(self, graph: int, level: int) -> np.ndarray:
+        n = self.stats(graph)["n"][level]
+        a = np.empty(n, dtype=np.int32)
+        _check(load().cmg_batch_get_aggregates(self._b, graph, level, C.c_void_p(a.ctypes.data)),
+               "batch_aggregates")
+        return a
+
+    def level_csr(self, graph: int, level: int):
+        st = self.stats(graph)
+        n, m = st["n"][level], st["nnz"][level]
+        rp = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(m, dtype=np.int32)
+        w = np.empty(m, dtype=np.float64)
+        g = C.c_double()
+        _check(load().cmg_batch_get_level_csr(self._b, graph, level, C.c_void_p(rp.ctypes.data),
+                                              C.c_void_p(col.ctypes.data), C.c_void_p(w.ctypes.data),
+                                              C.byref(g)), "batch_level_csr")
+        return rp, col, w, g.value
+
+    def set_replay(self, sweeps):
+        """sweeps: int array [G][64] (or None to return to opts.replay_sweeps)."""
+        if sweeps is None:
+            _check(load().cmg_batch_set_replay(self._b, None), "set_replay")
+            return
+        arr = np.zeros((self.G, CMG_MAX_LEVELS), dtype=np.int32)
+        for q, row in enumerate(sweeps):
+            arr[q, :len(row)] = row
+        _check(load().cmg_batch_set_replay(self._b, C.c_void_p(arr.ctypes.data)), "set_replay")
+
+    def shape(self, level: int):
+        sh = BatchShape()
+        _check(load().cmg_batch_config(self._b, level, 0, C.byref(sh)), "batch_config")
+        return sh.as_tuple()
+
+    def set_shape(self, level: int, threads_per_graph: int, lanes_per_row: int,
+                  graphs_per_cta: int, stage_csr: int = 1):
+        sh = BatchShape(threads_per_graph, lanes_per_row, graphs_per_cta, stage_csr)
+        _check(load().cmg_batch_config(self._b, level, 1, C.byref(sh)), "batch_config",
+               allow_warn=False)
+
+    def autotune(self, stream=None):
+        _check(load().cmg_batch_autotune(self._b, _stream(stream)), "batch_autotune", allow_warn=False)
+
+    def device_bytes(self) -> int:
+        b = C.c_size_t()
+        _check(load().cmg_batch_device_bytes(self._b, C.byref(b)), "batch_bytes")
+        return b.value
+
+    def fiedler(self, u_out=None, stream=None):
+        """Returns (u, lambda2[G], residual[G], status[G]); u is the union vector
+        (numpy on the host unless a torch CUDA tensor is passed)."""
+        if u_out is None:
+            u_out = np.empty(self.N, dtype=np.float64)
+        p_u, mem = _ptr(u_out)
+        lam = np.empty(self.G, dtype=np.float64)
+        res = np.empty(self.G, dtype=np.float64)
+        sts = np.empty(self.G, dtype=np.int32)
+        st = load().cmg_fiedler_batch(self._b, p_u, mem, C.c_void_p(lam.ctypes.data),
+                                      C.c_void_p(res.ctypes.data), C.c_void_p(sts.ctypes.data),
+                                      _stream(stream))
+        _check(st, "cmg_fiedler_batch")
+        return u_out, lam, res, sts
 
 
 # ------------------------------------------------------------------ step entry points

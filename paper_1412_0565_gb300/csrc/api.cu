@@ -134,7 +134,7 @@ static void free_hierarchy(cmg_hierarchy_s *h) {
     delete h;
 }
 
-static cmg_status_t check_options(const cmg_options_t &o) {
+cmg_status_t cmg::check_options(const cmg_options_t &o) {
     if (!(o.tol >= 0.0) || !(o.tol < 1.0)) return CMG_ERR_INVALID_ARG;
     if (o.coarse_size < 1 || o.max_levels < 1 || o.max_levels > CMG_MAX_LEVELS)
         return CMG_ERR_INVALID_ARG;
@@ -156,10 +156,9 @@ static cmg_status_t map_flags(unsigned f) {
     return CMG_OK;
 }
 
-static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t *row_ptr,
-                                    const int32_t *col, const double *w, int32_t mem) {
-    cudaStream_t s = h->stream;
-    const cmg_options_t &o = h->opts;
+cmg_status_t cmg::load_level0(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w,
+                              int32_t mem, int validate, int **rp_out, int **col_out,
+                              double **w_out, long long *nnz_out, cudaStream_t s) {
     // ---- nnz and size limits
     int64_t nnz = 0;
     if (mem == CMG_MEM_HOST) {
@@ -170,15 +169,12 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     }
     if (nnz < 0) return CMG_ERR_BAD_CSR;
     if (nnz >= 2147483647ll) return CMG_ERR_TOO_LARGE;
-    // ---- level 0: copy in (int64 row pointers converted on the device)
-    LevelData L0;
-    L0.n = (int)n;
-    L0.nnz = nnz;
-    h->lv.push_back(L0);
-    LevelData &Z = h->lv.back();
-    CMG_TRY(dev_alloc_n(&Z.rp, (size_t)n + 1, s));
-    CMG_TRY(dev_alloc_n(&Z.col, (size_t)std::max<int64_t>(nnz, 1), s));
-    CMG_TRY(dev_alloc_n(&Z.w, (size_t)std::max<int64_t>(nnz, 1), s));
+    *nnz_out = nnz;
+    // ---- copy in (int64 row pointers converted on the device); the caller
+    // owns the three arrays once they are allocated, also on error
+    CMG_TRY(dev_alloc_n(rp_out, (size_t)n + 1, s));
+    CMG_TRY(dev_alloc_n(col_out, (size_t)std::max<int64_t>(nnz, 1), s));
+    CMG_TRY(dev_alloc_n(w_out, (size_t)std::max<int64_t>(nnz, 1), s));
     Scratch scr(s);
     int64_t *rp64;
     unsigned *flags;
@@ -192,23 +188,43 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         rp64 = const_cast<int64_t *>(row_ptr);
     }
     if (nnz > 0) {
-        CMG_CUDA(cudaMemcpyAsync(Z.col, col, sizeof(int32_t) * (size_t)nnz, kind, s));
-        CMG_CUDA(cudaMemcpyAsync(Z.w, w, sizeof(double) * (size_t)nnz, kind, s));
+        CMG_CUDA(cudaMemcpyAsync(*col_out, col, sizeof(int32_t) * (size_t)nnz, kind, s));
+        CMG_CUDA(cudaMemcpyAsync(*w_out, w, sizeof(double) * (size_t)nnz, kind, s));
     }
     const int threads = 256;
-    k_check_rowptr<<<grid_for(n + 1, threads), threads, 0, s>>>((int)n, rp64, nnz, Z.rp, flags);
+    k_check_rowptr<<<grid_for(n + 1, threads), threads, 0, s>>>((int)n, rp64, nnz, *rp_out, flags);
     CMG_TRY(launch_status());
-    if (o.validate) {
+    if (validate) {
         unsigned hf = 0;
         CMG_CUDA(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CMG_CUDA(cudaStreamSynchronize(s));
         if (hf & kBadCsr) return CMG_ERR_BAD_CSR;
-        k_check_entries<<<grid_for(n, threads), threads, 0, s>>>((int)n, Z.rp, Z.col, Z.w, flags);
+        k_check_entries<<<grid_for(n, threads), threads, 0, s>>>((int)n, *rp_out, *col_out, *w_out, flags);
         CMG_TRY(launch_status());
         CMG_CUDA(cudaMemcpyAsync(&hf, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
         CMG_CUDA(cudaStreamSynchronize(s));
         CMG_TRY(map_flags(hf));
     }
+    return CMG_OK;
+}
+
+cmg_status_t cmg::launch_to_float(long long m, const double *w, float *w32, cudaStream_t s) {
+    if (m <= 0) return CMG_OK;
+    k_to_float<<<grid_for(m, 256), 256, 0, s>>>(m, w, w32);
+    return launch_status();
+}
+
+static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t *row_ptr,
+                                    const int32_t *col, const double *w, int32_t mem) {
+    cudaStream_t s = h->stream;
+    const cmg_options_t &o = h->opts;
+    // ---- level 0: copy in, validate
+    LevelData L0;
+    L0.n = (int)n;
+    h->lv.push_back(L0);
+    LevelData &Z = h->lv.back();
+    CMG_TRY(load_level0(n, row_ptr, col, w, mem, o.validate, &Z.rp, &Z.col, &Z.w, &Z.nnz, s));
+    Scratch scr(s);
     {
         double *gd;
         CMG_TRY(scr.get(&gd, 1));
@@ -287,10 +303,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     if (o.precision == CMG_PRECISION_FP32_SWEEP) {
         for (auto &L : h->lv) {
             CMG_TRY(dev_alloc_n(&L.w32, (size_t)std::max<long long>(L.nnz, 1), s));
-            if (L.nnz > 0) {
-                k_to_float<<<grid_for(L.nnz, threads), threads, 0, s>>>(L.nnz, L.w, L.w32);
-                CMG_TRY(launch_status());
-            }
+            CMG_TRY(launch_to_float(L.nnz, L.w, L.w32, s));
         }
     }
     // ---- row tiles (large levels) and SELL-32 sizes (small levels)

@@ -34,6 +34,8 @@ cmg_status_t from_cuda(cudaError_t e);
 // counts the launch.  Every kernel launch of the library is followed by it.
 cmg_status_t launch_status();
 unsigned long long launches_issued();
+// Adjusts the launch count (kernels replayed from a CUDA graph count when replayed).
+void add_launches(long long k);
 
 // ----------------------------------------------------------------- memory
 // Stream-ordered allocations from a library-owned pool on the current device.

@@ -69,6 +69,31 @@ __global__ void k_ranks(int n, uint64_t seed, int level, uint32_t *__restrict__ 
         r[v] = feistel_rank((uint32_t)v, (uint32_t)n, k / 2, key);
 }
 
+// Ranks of a block-diagonal union of graphs (vertex offsets voff[0..G]):
+// vertex v of graph q gets voff[q] + (its rank within graph q, level `level`).
+// Rank space is then graph-major, so HEC on the union numbers each graph's
+// aggregates contiguously and in that graph's own creator order.
+__global__ void k_ranks_batch(int n, int G, const int *__restrict__ voff, uint64_t seed, int level,
+                              uint32_t *__restrict__ r) {
+    uint64_t key[4];
+#pragma unroll
+    for (int t = 0; t < 4; t++)
+        key[t] = splitmix64(seed ^ ((uint64_t)(int64_t)level * 0x9E3779B97F4A7C15ull) ^ (uint64_t)t);
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;   // last q with voff[q] <= v
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(voff + mid) <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        const int v0 = __ldg(voff + lo);
+        const int ng = __ldg(voff + lo + 1) - v0;
+        int k = 2;
+        while ((1ll << k) < (long long)ng) k += 2;
+        r[v] = (uint32_t)v0 + feistel_rank((uint32_t)(v - v0), (uint32_t)ng, k / 2, key);
+    }
+}
+
 // Heaviest neighbour, G lanes per row: strict '>' on the weight, ties to the
 // lowest column (Alg. 2's argmin of the column of L).  -1 for an empty row.
 template <int G>
@@ -140,6 +165,14 @@ cmg_status_t launch_ranks(int n, uint64_t seed, int level, uint32_t *r, cudaStre
     if (n <= 0) return CMG_OK;
     const int threads = 256;
     k_ranks<<<grid_for(n, threads), threads, 0, s>>>(n, seed, level, r);
+    return launch_status();
+}
+
+cmg_status_t launch_ranks_batch(int n, int G, const int *voff, uint64_t seed, int level, uint32_t *r,
+                                cudaStream_t s) {
+    if (n <= 0) return CMG_OK;
+    const int threads = 256;
+    k_ranks_batch<<<grid_for(n, threads), threads, 0, s>>>(n, G, voff, seed, level, r);
     return launch_status();
 }
 

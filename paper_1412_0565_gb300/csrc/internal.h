@@ -23,6 +23,9 @@ cmg_status_t hec_level_async(int n, long long nnz, const int *rp, const int *col
 cmg_status_t launch_heaviest(int n, double avg, const int *rp, const int *col, const double *w,
                              int *m, cudaStream_t s);
 cmg_status_t launch_ranks(int n, uint64_t seed, int level, uint32_t *r, cudaStream_t s);
+// Ranks of a block-diagonal union of G graphs with vertex offsets voff (device).
+cmg_status_t launch_ranks_batch(int n, int G, const int *voff, uint64_t seed, int level, uint32_t *r,
+                                cudaStream_t s);
 
 // ---------------------------------------------------------------- primitives.cu
 // Exclusive scan of int32 in[0..n) into out[0..n]; out[n] = total (device).
@@ -36,6 +39,18 @@ cmg_status_t radix_sort_pairs(uint64_t **keys, uint32_t **vals, uint64_t *keys_a
                               Scratch &scr, cudaStream_t s);
 
 // ---------------------------------------------------------------- galerkin.cu
+// Option checks shared by the single-graph and batched setup.
+cmg_status_t check_options(const cmg_options_t &o);
+// Level 0 of a hierarchy: copies the CSR (host or device, int64 row pointers)
+// into new device arrays (int32 row pointers) and, with `validate`, checks
+// the input contract of cmg_setup.  The arrays belong to the caller as soon
+// as they are allocated, also when an error is returned.
+cmg_status_t load_level0(int64_t n, const int64_t *row_ptr, const int32_t *col, const double *w,
+                         int32_t mem, int validate, int **rp_out, int **col_out, double **w_out,
+                         long long *nnz_out, cudaStream_t s);
+// w32[k] = (float)w[k].
+cmg_status_t launch_to_float(long long m, const double *w, float *w32, cudaStream_t s);
+
 // Bits needed for the ids 0..c-1 (at least 1).
 inline int bits_for(int c) {
     int b = 1;

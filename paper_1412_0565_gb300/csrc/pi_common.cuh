@@ -1,0 +1,131 @@
+// pi_common.cuh -- device pieces shared by the power-iteration kernels of
+// the single-graph form (refine.cu) and the batched form (batch.cu): the
+// Gaussian start of Alg. 1 Step 2, float-float partial sums of one sweep, and
+// power-of-two rescaling helpers.
+#pragma once
+
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "ffloat.cuh"
+
+namespace cmg {
+
+constexpr float kZeroTol2_64 = 2.0194839e-28f;  // (64 eps_64)^2
+constexpr float kZeroTol2_32 = 5.8207661e-11f;  // (64 eps_32)^2
+
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+    uint64_t z = x + 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Alg. 1 Step 2's randn: Box-Muller on two splitmix64 uniforms in (0, 1]:
+// a = splitmix64(seed ^ 0xC0A45E ^ 2i), b = splitmix64(seed ^ 0xC0A45E ^ (2i+1)).
+__device__ __forceinline__ double gaussian_entry(uint64_t seed, long long i) {
+    const uint64_t a = sm64(seed ^ 0xC0A45Eull ^ (uint64_t)(2 * i));
+    const uint64_t b = sm64(seed ^ 0xC0A45Eull ^ (uint64_t)(2 * i + 1));
+    const double u1 = (double)((a >> 11) + 1) * (1.0 / 9007199254740992.0);
+    const double u2 = (double)((b >> 11) + 1) * (1.0 / 9007199254740992.0);
+    return sqrt(-2.0 * log(u1)) * cos(6.283185307179586476925286766559 * u2);
+}
+
+// ------------------------------------------------------------------ partial sums
+// A = sum y (the mean must be removed to rounding level relative to |y|, so
+// it needs float-float like B = sum y^2 and C = sum y y_prev, which decide
+// the stopping cosine).
+struct Part {
+    ff A, B, C;
+};
+
+__device__ __forceinline__ Part part_zero() {
+    Part p;
+    p.A = p.B = p.C = ff_zero();
+    return p;
+}
+
+__device__ __forceinline__ Part part_add(Part x, Part y) {
+    Part r;
+    r.A = ff_add_lazy(x.A, y.A);
+    r.B = ff_add_lazy(x.B, y.B);
+    r.C = ff_add_lazy(x.C, y.C);
+    return r;
+}
+
+// Sum over lanes 0, lo, 2 lo, ... (lo a power of two; lanes between hold
+// nothing), taking the xor tree from stride 16 down to lo in a fixed order.
+// The sum ends in lane 0 (and every lane of its residue class), renormalised.
+__device__ __forceinline__ Part warp_sum_part(Part p, int lo = 1, int width = 32) {
+    for (int o = width >> 1; o >= lo; o >>= 1) {
+        Part q;
+        q.A = shfl_xor_ff(p.A, o);
+        q.B = shfl_xor_ff(p.B, o);
+        q.C = shfl_xor_ff(p.C, o);
+        p = part_add(p, q);
+    }
+    p.A = ff_norm(p.A);
+    p.B = ff_norm(p.B);
+    p.C = ff_norm(p.C);
+    return p;
+}
+
+__device__ __forceinline__ int pow2_at_least(int v) {
+    int w = 1;
+    while (w < v) w <<= 1;
+    return w;
+}
+
+// Per-thread accumulation of (sum y, sum y^2, sum y x) for one sweep.
+template <typename T>
+struct Acc;
+
+template <>
+struct Acc<float> {
+    ff A, B, C;
+    __device__ __forceinline__ void reset() { A = B = C = ff_zero(); }
+    __device__ __forceinline__ void add(float y, float x) {
+        A = ff_add_lazy(A, ff_make(y, 0.f));
+        B = ff_add_lazy(B, two_prod(y, y));
+        C = ff_add_lazy(C, two_prod(y, x));
+    }
+    __device__ __forceinline__ Part get() const {
+        Part p;
+        p.A = ff_norm(A);
+        p.B = ff_norm(B);
+        p.C = ff_norm(C);
+        return p;
+    }
+};
+
+template <>
+struct Acc<double> {
+    double A, B, C;
+    __device__ __forceinline__ void reset() { A = B = C = 0.0; }
+    __device__ __forceinline__ void add(double y, double x) {
+        A += y;
+        B = fma(y, y, B);
+        C = fma(y, x, C);
+    }
+    __device__ __forceinline__ Part get() const {
+        Part p;
+        p.A = ff_from_double(A);
+        p.B = ff_from_double(B);
+        p.C = ff_from_double(C);
+        return p;
+    }
+};
+
+__device__ __forceinline__ double to_d(ff a) { return ff_to_double(a); }
+
+__device__ __forceinline__ int start_exponent(double ss0) {
+    // 2^e0 ~ 1 / ||proj y_0||
+    if (!(ss0 > 0.0)) return 0;
+    return -(int)floor(0.5 * log2(ss0) + 0.5);
+}
+
+// x * 2^e for a normal float x and a small e (exponent arithmetic, exact).
+__device__ __forceinline__ float scale2f(float x, int e) { return __int_as_float(__float_as_int(x) + (e << 23)); }
+
+}  // namespace cmg

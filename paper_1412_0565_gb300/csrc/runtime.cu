@@ -25,6 +25,8 @@ cmg_status_t launch_status() {
 
 unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
 
+void add_launches(long long k) { g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed); }
+
 // ----------------------------------------------------------------- memory pool
 namespace {
 constexpr int kMaxDevices = 64;

@@ -74,3 +74,29 @@ def test_estimate_device_bytes_monotone():
     b = cmg.estimate_device_bytes(1_000_000, 6_000_000)
     assert 0 < a < b
     assert cmg.estimate_device_bytes(10**6, 6 * 10**6, cmg.FP32_SWEEP) > 0
+
+
+def test_batch_host_side_argument_errors_need_no_gpu():
+    lib = cmg.load()
+    b = C.c_void_p()
+    rp = np.array([0, 0], dtype=np.int64)
+    col = np.zeros(1, dtype=np.int32)
+    w = np.ones(1)
+    P = lambda a: C.c_void_p(a.ctypes.data)
+
+    def setup(offs, mem=0, opts=None, G=None):
+        offs = np.asarray(offs, dtype=np.int64)
+        return cmg.STATUS[lib.cmg_setup_batch(len(offs) - 1 if G is None else G, P(offs), P(rp),
+                                              P(col), P(w), mem, opts, None, C.byref(b))]
+
+    assert setup([0, 4, 5]) == "ERR_TOO_SMALL"          # graph 1 has one vertex
+    assert setup([0, 4, 3, 8]) == "ERR_INVALID_ARG"     # decreasing offsets
+    assert setup([1, 4, 8]) == "ERR_INVALID_ARG"        # does not start at 0
+    assert setup([0, 4, 8], G=0) == "ERR_INVALID_ARG"
+    assert setup([0, 4, 8], mem=3) == "ERR_INVALID_ARG"
+    bad = cmg.options(coarse_size=0)
+    assert setup([0, 4, 8], opts=C.byref(bad)) == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_fiedler_batch(None, None, 0, None, None, None, None)] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_batch_free(None)] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_batch_stats(None, 0, None)] == "ERR_INVALID_ARG"
+    assert not b.value

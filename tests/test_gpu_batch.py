@@ -1,0 +1,229 @@
+"""Batched form: every graph of a batch against the CPU oracle run on that
+graph alone.
+
+The batch shares one block-diagonal union per level, so these tests check
+that nothing leaks between graphs: per graph, the hierarchy (sizes, CSR,
+aggregates, shifts) equals the oracle's bit for bit, the FP64 vector is
+within 1e-10 relative 2-norm and lambda2 within 1e-12 relative, with the
+same per-level sweep counts, for every launch shape; the FP32 sweep form
+meets lambda2 <= 1e-6 relative and angle <= 1e-4 rad in replay mode.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1412_0565_gb300 import cmg, inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VEC_TOL = 1e-10
+LAM_TOL = 1e-12
+SEED = 1412
+
+
+def aligned_err(u, ref):
+    if np.dot(u, ref) < 0:
+        u = -u
+    return np.linalg.norm(u - ref) / np.linalg.norm(ref)
+
+
+def angle(u, ref):
+    c = abs(np.dot(u, ref)) / (np.linalg.norm(u) * np.linalg.norm(ref))
+    return float(np.arccos(min(1.0, c)))
+
+
+def mixed_graphs():
+    """Uneven sizes and every way a graph leaves the cascade: n <= 25 from
+    the start (J = 0), collapse to one aggregate (star), n = 2, and graphs
+    whose iterates do not fit in shared memory in the FP64 form."""
+    return [
+        inputs.rgg(800, 8.0, seed=21),
+        inputs.grid2d(30, 40, "uniform", seed=22),
+        inputs.barabasi_albert(1500, 4, seed=23),
+        inputs.path(40),
+        inputs.cycle(30),
+        inputs.random_connected(3000, 9000, seed=24),
+        inputs.grid2d(7, 3, "uniform", seed=25),
+        inputs.path(2, [0.75]),
+        inputs.star(100),
+        inputs.complete(30),
+        inputs.rgg(6000, 8.0, seed=26),
+        inputs.random_connected(2500, 5000, seed=27, ties=True),
+        inputs.barabasi_albert(700, 4, seed=28),
+    ]
+
+
+@pytest.fixture(scope="module")
+def batch_case():
+    graphs = mixed_graphs()
+    rp, col, w, offs = inputs.concat_csr(graphs)
+    refs = [oracle.fiedler(g[0], g[1], g[2], seed=SEED) for g in graphs]
+    return graphs, (rp, col, w, offs), refs
+
+
+def check_fp64(b, graphs, refs, u, lam, res):
+    offs = b.offsets
+    for q, (g, ref) in enumerate(zip(graphs, refs)):
+        ref_u, ref_lam, ref_res, oh, rr = ref
+        st = b.stats(q)
+        assert st["n"] == oh.sizes(), q
+        assert st["sweeps"] == rr["sweeps"].tolist(), q
+        uq = u[offs[q]:offs[q + 1]]
+        assert aligned_err(uq, ref_u) <= VEC_TOL, q
+        assert abs(lam[q] - ref_lam) <= LAM_TOL * abs(ref_lam), q
+        assert res[q] == pytest.approx(ref_res, rel=1e-6, abs=1e-13), q
+        # output contract per graph
+        assert abs(np.linalg.norm(uq) - 1.0) <= 1e-13
+        assert abs(uq.sum()) <= 1e-12 * np.sqrt(len(uq))
+        assert uq[int(np.argmax(np.abs(uq)))] > 0
+
+
+def test_batch_hierarchy_matches_oracle(batch_case):
+    graphs, (rp, col, w, offs), refs = batch_case
+    with cmg.Batch(offs, rp, col, w, seed=SEED) as b:
+        assert b.G == len(graphs)
+        for q, ref in enumerate(refs):
+            oh = ref[3]
+            st = b.stats(q)
+            assert st["levels"] == oh.levels
+            assert st["n"] == oh.sizes()
+            for lvl in range(oh.levels):
+                brp, bcol, bw, bg = b.level_csr(q, lvl)
+                orp, ocol, ow = oh.csr(lvl)
+                assert np.array_equal(brp, orp) and np.array_equal(bcol, ocol), (q, lvl)
+                assert np.array_equal(bw.view(np.uint64), ow.view(np.uint64)), (q, lvl)
+                assert bg == oh.info(lvl)[2], (q, lvl)
+                if lvl + 1 < oh.levels:
+                    assert np.array_equal(b.aggregates(q, lvl), oh.agg(lvl)), (q, lvl)
+        # J = 0 cases: n <= 25, n = 2, and the star's collapse
+        for q in (6, 7, 8):
+            assert b.stats(q)["levels"] == 1
+
+
+SHAPES = [
+    None,                  # default shapes
+    (32, 1, 4, 1),
+    (32, 4, 8, 0),
+    (64, 2, 2, 1),
+    (128, 1, 2, 0),
+    (128, 8, 1, 1),
+    (256, 16, 2, 1),
+    (512, 32, 1, 0),
+]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "default" if s is None else "x".join(map(str, s)))
+def test_batch_fp64_matches_oracle(batch_case, shape):
+    graphs, (rp, col, w, offs), refs = batch_case
+    with cmg.Batch(offs, rp, col, w, seed=SEED) as b:
+        if shape is not None:
+            for lvl in range(b.union_levels):
+                b.set_shape(lvl, *shape)
+        u, lam, res, sts = b.fiedler()
+        assert (sts == 0).all()
+        check_fp64(b, graphs, refs, u, lam, res)
+
+
+def test_batch_device_buffers_and_replayed_graph(batch_case):
+    """Device inputs and outputs on a side stream; repeated solves replay the
+    captured CUDA graph and give identical bits."""
+    graphs, (rp, col, w, offs), refs = batch_case
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        drp = torch.from_numpy(rp).cuda()
+        dcol = torch.from_numpy(col).cuda()
+        dw = torch.from_numpy(w).cuda()
+        b = cmg.Batch(offs, drp, dcol, dw, seed=SEED, stream=s.cuda_stream)
+        u = torch.empty(len(rp) - 1, dtype=torch.float64, device="cuda")
+        _, lam, res, _ = b.fiedler(u_out=u, stream=s.cuda_stream)
+        u1 = u.cpu().numpy().copy()
+        for _ in range(3):
+            _, lam2, _, _ = b.fiedler(u_out=u, stream=s.cuda_stream)
+            assert np.array_equal(u.cpu().numpy(), u1) and np.array_equal(lam, lam2)
+    s.synchronize()
+    check_fp64(b, graphs, refs, u1, lam, res)
+    b.close()
+
+
+def test_batch_autotune_keeps_results(batch_case):
+    graphs, (rp, col, w, offs), refs = batch_case
+    with cmg.Batch(offs, rp, col, w, seed=SEED) as b:
+        b.autotune()
+        for lvl in range(b.union_levels):
+            tpg, lpr, gpc, stage = b.shape(lvl)
+            assert 32 <= tpg <= 512 and lpr in (1, 2, 4, 8, 16, 32) and tpg * gpc <= 512
+        u, lam, res, _ = b.fiedler()
+        check_fp64(b, graphs, refs, u, lam, res)
+
+
+def test_batch_fp32_replay_accuracy(batch_case):
+    """FP32 sweeps with the oracle's per-level counts: precision alone."""
+    graphs, (rp, col, w, offs), refs = batch_case
+    with cmg.Batch(offs, rp, col, w, seed=SEED, precision="fp32", schedule="replay") as b:
+        b.set_replay([r[4]["sweeps"].tolist() for r in refs])
+        u, lam, res, _ = b.fiedler()
+        for q, ref in enumerate(refs):
+            ref_u, ref_lam = ref[0], ref[1]
+            assert b.stats(q)["sweeps"] == ref[4]["sweeps"].tolist()
+            uq = u[offs[q]:offs[q + 1]]
+            assert abs(lam[q] - ref_lam) <= 1e-6 * abs(ref_lam), q
+            assert angle(uq, ref_u) <= 1e-4, q
+
+
+def test_batch_fp32_tolerance_mode(batch_case):
+    """FP32 sweep form in the default mode: stated accuracy against the FP64
+    oracle (sweep counts may differ by rounding of the stop test)."""
+    graphs, (rp, col, w, offs), refs = batch_case
+    with cmg.Batch(offs, rp, col, w, seed=SEED, precision="fp32") as b:
+        u, lam, res, _ = b.fiedler()
+        for q, ref in enumerate(refs):
+            uq = u[offs[q]:offs[q + 1]]
+            assert abs(lam[q] - ref[1]) <= 1e-6 * abs(ref[1]), q
+            assert angle(uq, ref[0]) <= 1e-4, q
+
+
+def test_batch_fixed_schedule_matches_oracle():
+    graphs = [inputs.grid2d(40, 30, "uniform", seed=31), inputs.rgg(1200, 8.0, seed=32),
+              inputs.path(60)]
+    rp, col, w, offs = inputs.concat_csr(graphs)
+    with cmg.Batch(offs, rp, col, w, seed=3, schedule="fixed", beta=2.0, k0=2) as b:
+        u, lam, _, _ = b.fiedler()
+        for q, (grp, gcol, gw) in enumerate(graphs):
+            oh = oracle.Hierarchy(grp, gcol, gw, seed=3)
+            ref = oh.solve(schedule="fixed", beta=2.0, k0=2)
+            assert b.stats(q)["sweeps"] == ref["sweeps"].tolist()
+            assert aligned_err(u[offs[q]:offs[q + 1]], ref["u"]) <= VEC_TOL
+            assert abs(lam[q] - ref["lam"]) <= LAM_TOL * abs(ref["lam"])
+
+
+def test_batch_single_graph_equals_plain_path():
+    rp, col, w = inputs.grid2d(64, 64, "unit")
+    offs = np.array([0, len(rp) - 1], dtype=np.int64)
+    with cmg.Batch(offs, rp, col, w, seed=SEED) as b:
+        u, lam, _, _ = b.fiedler()
+    h = cmg.Hierarchy(rp, col, w, seed=SEED)
+    u2, lam2, st2 = h.fiedler()
+    assert aligned_err(u, u2) <= VEC_TOL
+    assert abs(lam[0] - lam2) <= LAM_TOL * lam2
+    h.close()
+
+
+def test_batch_input_errors():
+    g1 = inputs.path(10)
+    g2 = inputs.cycle(12)
+    rp, col, w, offs = inputs.concat_csr([g1, g2])
+    # an entry that joins the two graphs
+    bad = col.copy()
+    bad[-1] = 0
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.Batch(offs, rp, bad, w)
+    assert e.value.status in (-10, -2)   # BAD_CSR (or the broken symmetry)
+    # a one-vertex graph
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.Batch(np.array([0, 1, 22]), rp, col, w)
+    assert e.value.name == "ERR_TOO_SMALL"
+    # offsets that decrease / do not start at 0
+    with pytest.raises(cmg.CmgError) as e:
+        cmg.Batch(np.array([0, 12, 10, 22]), rp, col, w)
+    assert e.value.name == "ERR_INVALID_ARG"
