@@ -256,6 +256,12 @@ typedef struct cmg_batch_shape {
 cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t set, cmg_batch_shape_t *shape);
 cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream);
 
+/* Device time of union level `level`'s power-iteration launch in the last
+ * cmg_fiedler_batch, when options.timing = 1 (the launches are then issued
+ * one by one with CUDA events instead of replaying the captured graph);
+ * else 0. */
+cmg_status_t cmg_batch_level_ms(cmg_batch_t b, int32_t level, double *ms);
+
 /* Device bytes held by the batch (levels and solve workspace). */
 cmg_status_t cmg_batch_device_bytes(cmg_batch_t b, size_t *bytes);
 

@@ -39,7 +39,8 @@ EXPORTS = [
     "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
     "cmg_setup_batch", "cmg_fiedler_batch", "cmg_batch_info", "cmg_batch_stats",
     "cmg_batch_get_aggregates", "cmg_batch_get_level_csr", "cmg_batch_set_replay",
-    "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_device_bytes", "cmg_batch_free",
+    "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
+    "cmg_batch_free",
 ]
 
 NOALLOC_MAX_N = 262144
@@ -135,6 +136,7 @@ def load(build_if_stale: bool = True):
             "cmg_batch_set_replay": (I32, [V, V]),
             "cmg_batch_config": (I32, [V, I32, I32, P(BatchShape)]),
             "cmg_batch_autotune": (I32, [V, V]),
+            "cmg_batch_level_ms": (I32, [V, I32, P(F64)]),
             "cmg_batch_device_bytes": (I32, [V, P(C.c_size_t)]),
             "cmg_batch_free": (I32, [V]),
         }
@@ -411,6 +413,15 @@ class Batch:
 
     def autotune(self, stream=None):
         _check(load().cmg_batch_autotune(self._b, _stream(stream)), "batch_autotune", allow_warn=False)
+
+    def level_ms(self):
+        """Per-union-level device times of the last solve (options timing=1)."""
+        out = []
+        for lvl in range(self.union_levels):
+            ms = C.c_double()
+            _check(load().cmg_batch_level_ms(self._b, lvl, C.byref(ms)), "batch_level_ms")
+            out.append(ms.value)
+        return out
 
     def device_bytes(self) -> int:
         b = C.c_size_t()

@@ -661,6 +661,7 @@ struct cmg_batch_s {
     cudaGraphExec_t exec = nullptr;
     bool dirty = true;
     unsigned long long graph_kernels = 0;
+    std::vector<double> level_ms;     // options.timing: device time per union level
     size_t bytes = 0;
 };
 
@@ -1134,10 +1135,30 @@ extern "C" cmg_status_t cmg_fiedler_batch(cmg_batch_t b, double *u_out, int32_t 
     if (u_out && u_mem != CMG_MEM_HOST && u_mem != CMG_MEM_DEVICE) return CMG_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     cudaStream_t s = (cudaStream_t)stream;
-    if (b->dirty) CMG_TRY(capture(b));
-    CMG_CUDA(cudaGraphLaunch(b->exec, s));
-    add_launches((long long)b->graph_kernels);
     const int G = b->G, L = (int)b->lv.size();
+    if (b->opts.timing) {
+        // eager launches with an event pair around each level
+        std::vector<cudaEvent_t> ev(2 * L);
+        for (auto &e : ev) CMG_CUDA(cudaEventCreate(&e));
+        cmg_status_t st = from_cuda(cudaMemsetAsync(b->queue, 0, sizeof(int) * L, s));
+        for (int j = L - 1; j >= 0 && st == CMG_OK; j--) {
+            cudaEventRecord(ev[2 * j], s);
+            st = launch_level(b, j, -1, s);
+            cudaEventRecord(ev[2 * j + 1], s);
+        }
+        if (st == CMG_OK) st = from_cuda(cudaStreamSynchronize(s));
+        b->level_ms.assign(L, 0.0);
+        for (int j = 0; j < L && st == CMG_OK; j++) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]) == cudaSuccess) b->level_ms[j] = ms;
+        }
+        for (auto &e : ev) cudaEventDestroy(e);
+        CMG_TRY(st);
+    } else {
+        if (b->dirty) CMG_TRY(capture(b));
+        CMG_CUDA(cudaGraphLaunch(b->exec, s));
+        add_launches((long long)b->graph_kernels);
+    }
     b->h_sweeps.resize((size_t)L * G);
     b->h_flags.resize((size_t)L * G);
     b->h_cos.resize((size_t)L * G);
@@ -1360,6 +1381,12 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
     cudaEventDestroy(e1);
     drop_graph(b);
     return st;
+}
+
+extern "C" cmg_status_t cmg_batch_level_ms(cmg_batch_t b, int32_t level, double *ms) {
+    if (!b || !ms || level < 0 || level >= (int)b->lv.size()) return CMG_ERR_INVALID_ARG;
+    *ms = level < (int)b->level_ms.size() ? b->level_ms[level] : 0.0;
+    return CMG_OK;
 }
 
 extern "C" cmg_status_t cmg_batch_device_bytes(cmg_batch_t b, size_t *bytes) {

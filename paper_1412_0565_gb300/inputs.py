@@ -261,23 +261,49 @@ def concat_csr(graphs):
     return rp_all, col_all, w_all, offs
 
 
-def batch_graphs(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412):
+def _family_graph(i: int, nv: int, seed: int):
+    """Graph i of a mixed batch: families round-robin (random geometric graph
+    with mean degree 8, near-square 2D grid, Barabasi-Albert m=4), weights
+    U[0.5, 1.5], seeded by (seed, i)."""
+    fam = i % 3
+    s = int(seed * 100003 + i)
+    if fam == 0:
+        return rgg(int(nv), 8.0, seed=s)
+    if fam == 1:
+        a = int(np.floor(np.sqrt(nv)))
+        return grid2d(a, int(np.ceil(nv / a)), weights="uniform", seed=s)
+    return barabasi_albert(int(nv), 4, seed=s)
+
+
+def _family_chunk(args):
+    seed, items = args
+    return [_family_graph(i, nv, seed) for i, nv in items]
+
+
+def batch_sizes(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412):
+    """Vertex counts of a mixed batch: log-uniform in [lo, hi]."""
+    rng = np.random.default_rng(seed)
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
+
+
+def batch_graphs(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412,
+                 workers: int = 0):
     """Mixed batch: sizes log-uniform in [lo, hi]; families round-robin
     (random geometric graph with mean degree 8, near-square 2D grid, Barabasi-Albert
-    m=4); weights U[0.5, 1.5].  Returns a list of CSR triples."""
-    rng = np.random.default_rng(seed)
-    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
-    out = []
-    for i, nv in enumerate(sizes):
-        fam = i % 3
-        s = int(seed * 100003 + i)
-        if fam == 0:
-            out.append(rgg(int(nv), 8.0, seed=s))
-        elif fam == 1:
-            a = int(np.floor(np.sqrt(nv)))
-            out.append(grid2d(a, int(np.ceil(nv / a)), weights="uniform", seed=s))
-        else:
-            out.append(barabasi_albert(int(nv), 4, seed=s))
+    m=4); weights U[0.5, 1.5].  Returns a list of CSR triples.  workers > 1
+    generates in that many spawned processes (same graphs)."""
+    sizes = batch_sizes(count, lo, hi, seed)
+    items = [(i, int(nv)) for i, nv in enumerate(sizes)]
+    if workers <= 1:
+        return _family_chunk((seed, items))
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    chunks = [items[k::workers] for k in range(workers)]
+    out = [None] * count
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for chunk, res in zip(chunks, ex.map(_family_chunk, [(seed, c) for c in chunks])):
+            for (i, _), g in zip(chunk, res):
+                out[i] = g
     return out
 
 
