@@ -269,6 +269,75 @@ cmg_status_t cmg_batch_device_bytes(cmg_batch_t b, size_t *bytes);
 cmg_status_t cmg_batch_free(cmg_batch_t b);
 
 /* ------------------------------------------------------------------------
+ * Serving: a request loop for Fiedler solves.  The paper has no
+ * counterpart; it runs Alg. 1 for a stream of requests on one GPU.
+ *
+ * Graphs are registered once (host CSR, borrowed: the arrays must stay valid
+ * and unchanged until cmg_server_destroy).  A request names a graph and
+ * receives its vector, lambda2 and residual.  `workers` host threads, each
+ * with its own CUDA stream, run jobs so that their device work overlaps.  A
+ * job starts only when its device memory (cmg_estimate_device_bytes per
+ * graph; the exact size for a resident hierarchy) fits in `mem_budget`;
+ * idle resident hierarchies are evicted least recently used first to make
+ * room, and a request that can never fit fails with CMG_ERR_TOO_LARGE.
+ * Jobs: a graph with a resident hierarchy is solved with cmg_fiedler
+ * (warm); a graph with n > batch_max_n is set up with cmg_setup, solved and
+ * (keep_resident) kept; every pending request for a smaller graph without a
+ * hierarchy, up to max_batch, joins one batched job (cmg_setup_batch +
+ * cmg_fiedler_batch), so requests arriving while others run are admitted
+ * together as soon as a worker and memory free up.  Pending requests are
+ * taken first-fit in arrival order.  All requests use the server's options.
+ * ---------------------------------------------------------------------- */
+typedef struct cmg_server_s *cmg_server_t;
+
+typedef struct cmg_server_config {
+    int32_t workers;       /* concurrent jobs, 1..64 (4)                              */
+    int32_t max_batch;     /* graphs per batched job; 1 disables batching (256)       */
+    int64_t batch_max_n;   /* graphs with n <= batch_max_n are batched (50000)        */
+    uint64_t mem_budget;   /* device bytes for jobs and resident hierarchies;
+                              0 = 80% of the free device memory at creation          */
+    int32_t keep_resident; /* keep single-form hierarchies after their solve (1)      */
+    int32_t reserved;      /* must be 0                                               */
+} cmg_server_config_t;
+
+typedef struct cmg_request {
+    int32_t status;        /* CMG_OK, CMG_WARN_MAXITER or the error of the job        */
+    int32_t batch_size;    /* graphs in the job that solved the request (1 = alone)   */
+    int32_t warm;          /* 1: the hierarchy was resident (solve only)              */
+    int32_t pad;
+    double lambda2;
+    double residual;
+    uint64_t submit_ns, admit_ns, done_ns;  /* host steady clock                      */
+} cmg_request_t;
+
+typedef struct cmg_server_stats {
+    int64_t completed, single_jobs, batch_jobs, warm_jobs, evictions, resident;
+    uint64_t peak_bytes;   /* most device bytes reserved at once                     */
+    uint64_t used_bytes;   /* reserved now (running jobs + resident hierarchies)     */
+    uint64_t budget_bytes;
+} cmg_server_stats_t;
+
+/* workers 4, max_batch 256, batch_max_n 50000, mem_budget 0, keep_resident 1. */
+cmg_status_t cmg_server_config_default(cmg_server_config_t *cfg);
+/* Starts the workers on the current device.  opts: NULL = defaults
+ * (options.timing must be 0).  Errors: INVALID_ARG, CUDA. */
+cmg_status_t cmg_server_create(const cmg_server_config_t *cfg, const cmg_options_t *opts,
+                               cmg_server_t *out);
+/* Registers a graph (host CSR as for cmg_setup, borrowed); *graph_id
+ * receives its id.  The input contract is checked when a job sets it up. */
+cmg_status_t cmg_server_add_graph(cmg_server_t s, int64_t n, const int64_t *row_ptr,
+                                  const int32_t *col, const double *w, int64_t *graph_id);
+/* Queues a solve of graph `graph_id`; u_out (host double[n], nullable) must
+ * stay valid until the request completes.  *ticket identifies it. */
+cmg_status_t cmg_server_submit(cmg_server_t s, int64_t graph_id, double *u_out, int64_t *ticket);
+/* Blocks until the request completes; fills *out (nullable) and returns the
+ * request's status.  A ticket can be waited for once. */
+cmg_status_t cmg_server_wait(cmg_server_t s, int64_t ticket, cmg_request_t *out);
+cmg_status_t cmg_server_get_stats(cmg_server_t s, cmg_server_stats_t *out);
+/* Finishes every queued request, stops the workers, frees the hierarchies. */
+cmg_status_t cmg_server_destroy(cmg_server_t s);
+
+/* ------------------------------------------------------------------------
  * Step entry points.  Each runs one step of the method on DEVICE buffers in
  * the library's internal layout (row_ptr as int32[n+1]) on `stream`; they
  * exist so every step can be checked on its own.  Inputs are assumed to meet

@@ -40,7 +40,8 @@ EXPORTS = [
     "cmg_setup_batch", "cmg_fiedler_batch", "cmg_batch_info", "cmg_batch_stats",
     "cmg_batch_get_aggregates", "cmg_batch_get_level_csr", "cmg_batch_set_replay",
     "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
-    "cmg_batch_free",
+    "cmg_batch_free", "cmg_server_config_default", "cmg_server_create", "cmg_server_add_graph",
+    "cmg_server_submit", "cmg_server_wait", "cmg_server_get_stats", "cmg_server_destroy",
 ]
 
 NOALLOC_MAX_N = 262144
@@ -88,6 +89,32 @@ class BatchShape(C.Structure):
 
     def as_tuple(self):
         return (self.threads_per_graph, self.lanes_per_row, self.graphs_per_cta, self.stage_csr)
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("workers", C.c_int32), ("max_batch", C.c_int32), ("batch_max_n", C.c_int64),
+                ("mem_budget", C.c_uint64), ("keep_resident", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Request(C.Structure):
+    _fields_ = [("status", C.c_int32), ("batch_size", C.c_int32), ("warm", C.c_int32),
+                ("pad", C.c_int32), ("lambda2", C.c_double), ("residual", C.c_double),
+                ("submit_ns", C.c_uint64), ("admit_ns", C.c_uint64), ("done_ns", C.c_uint64)]
+
+    def as_dict(self):
+        return {"status": STATUS.get(self.status, self.status), "batch_size": self.batch_size,
+                "warm": bool(self.warm), "lambda2": self.lambda2, "residual": self.residual,
+                "latency_ms": (self.done_ns - self.submit_ns) / 1e6,
+                "queue_ms": (self.admit_ns - self.submit_ns) / 1e6}
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("completed", C.c_int64), ("single_jobs", C.c_int64), ("batch_jobs", C.c_int64),
+                ("warm_jobs", C.c_int64), ("evictions", C.c_int64), ("resident", C.c_int64),
+                ("peak_bytes", C.c_uint64), ("used_bytes", C.c_uint64), ("budget_bytes", C.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 def lib_path() -> str:
@@ -139,6 +166,13 @@ def load(build_if_stale: bool = True):
             "cmg_batch_level_ms": (I32, [V, I32, P(F64)]),
             "cmg_batch_device_bytes": (I32, [V, P(C.c_size_t)]),
             "cmg_batch_free": (I32, [V]),
+            "cmg_server_config_default": (I32, [P(ServerConfig)]),
+            "cmg_server_create": (I32, [P(ServerConfig), P(Options), P(V)]),
+            "cmg_server_add_graph": (I32, [V, I64, V, V, V, P(I64)]),
+            "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
+            "cmg_server_wait": (I32, [V, I64, P(Request)]),
+            "cmg_server_get_stats": (I32, [V, P(ServerStats)]),
+            "cmg_server_destroy": (I32, [V]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -442,6 +476,72 @@ class Batch:
                                       _stream(stream))
         _check(st, "cmg_fiedler_batch")
         return u_out, lam, res, sts
+
+
+class Server:
+    """Request loop for Fiedler solves (cmg_server_*): register host graphs,
+    submit requests, wait for results.  Graph arrays are kept alive here."""
+
+    def __init__(self, *, workers=4, max_batch=256, batch_max_n=50000, mem_budget=0,
+                 keep_resident=1, opts: Options | None = None, **kw):
+        lib = load()
+        cfg = ServerConfig()
+        _check(lib.cmg_server_config_default(C.byref(cfg)), "server_config")
+        cfg.workers, cfg.max_batch, cfg.batch_max_n = workers, max_batch, batch_max_n
+        cfg.mem_budget, cfg.keep_resident = mem_budget, keep_resident
+        self.opts = opts if opts is not None else options(**kw)
+        s = C.c_void_p()
+        self._s = None
+        _check(lib.cmg_server_create(C.byref(cfg), C.byref(self.opts), C.byref(s)), "server_create",
+               allow_warn=False)
+        self._s = s
+        self._graphs = []
+        self._outs = {}
+
+    def add_graph(self, row_ptr, col, w) -> int:
+        row_ptr, col, w = _as_inputs(np.asarray(row_ptr), np.asarray(col), np.asarray(w))
+        gid = C.c_int64()
+        _check(load().cmg_server_add_graph(self._s, len(row_ptr) - 1, C.c_void_p(row_ptr.ctypes.data),
+                                           C.c_void_p(col.ctypes.data), C.c_void_p(w.ctypes.data),
+                                           C.byref(gid)), "server_add_graph", allow_warn=False)
+        self._graphs.append((row_ptr, col, w))
+        return gid.value
+
+    def submit(self, graph_id: int, want_vector: bool = True) -> int:
+        n = len(self._graphs[graph_id][0]) - 1
+        u = np.empty(n, dtype=np.float64) if want_vector else None
+        t = C.c_int64()
+        _check(load().cmg_server_submit(self._s, graph_id,
+                                        C.c_void_p(u.ctypes.data) if u is not None else None,
+                                        C.byref(t)), "server_submit", allow_warn=False)
+        self._outs[t.value] = u
+        return t.value
+
+    def wait(self, ticket: int):
+        """Returns (u or None, request dict); raises on a failed request."""
+        r = Request()
+        st = load().cmg_server_wait(self._s, ticket, C.byref(r))
+        u = self._outs.pop(ticket, None)
+        _check(st, "server_wait")
+        return u, r.as_dict()
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        _check(load().cmg_server_get_stats(self._s, C.byref(s)), "server_stats")
+        return s.as_dict()
+
+    def close(self):
+        if getattr(self, "_s", None):
+            load().cmg_server_destroy(self._s)
+            self._s = None
+
+    __del__ = close
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 # ------------------------------------------------------------------ step entry points

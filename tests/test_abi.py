@@ -100,3 +100,27 @@ def test_batch_host_side_argument_errors_need_no_gpu():
     assert cmg.STATUS[lib.cmg_batch_free(None)] == "ERR_INVALID_ARG"
     assert cmg.STATUS[lib.cmg_batch_stats(None, 0, None)] == "ERR_INVALID_ARG"
     assert not b.value
+
+
+def test_server_argument_errors_need_no_gpu():
+    lib = cmg.load()
+    s = C.c_void_p()
+    cfg = cmg.ServerConfig()
+    assert lib.cmg_server_config_default(C.byref(cfg)) == 0
+    assert cfg.workers == 4 and cfg.max_batch == 256 and cfg.keep_resident == 1
+    for field, bad in (("workers", 0), ("workers", 65), ("max_batch", 0), ("reserved", 1)):
+        c2 = cmg.ServerConfig.from_buffer_copy(cfg)
+        setattr(c2, field, bad)
+        assert cmg.STATUS[lib.cmg_server_create(C.byref(c2), None, C.byref(s))] == "ERR_INVALID_ARG"
+    o = cmg.options(timing=1)
+    assert cmg.STATUS[lib.cmg_server_create(C.byref(cfg), C.byref(o), C.byref(s))] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_server_destroy(None)] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_server_wait(None, 1, None)] == "ERR_INVALID_ARG"
+    assert not s.value
+
+
+def test_public_structs_match_header_sizes():
+    assert C.sizeof(cmg.BatchShape) == 16
+    assert C.sizeof(cmg.ServerConfig) == 4 + 4 + 8 + 8 + 4 + 4
+    assert C.sizeof(cmg.Request) == 16 + 16 + 24
+    assert C.sizeof(cmg.ServerStats) == 6 * 8 + 3 * 8
