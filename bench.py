@@ -303,6 +303,13 @@ def run_gpu(args):
         e2e_tot = float(t.item())
     e2e_val = world * len(e2e_ms) / (e2e_tot / 1e3)
 
+    batch = None
+    if not args.no_batch and world == 1:
+        batch = run_batch(args, stream, flush)
+    serving = None
+    if not args.no_serving and world == 1:
+        serving = run_serving(args)
+
     if rank == 0:
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
@@ -344,11 +351,187 @@ def run_gpu(args):
                     "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n},
             "gpu_launches": r32["launches"],
             "clocks": clocks,
+            "batch": batch,
+            "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+BATCH_WORKLOAD = ("4096 graphs, n log-uniform [500, 20000], random geometric (mean degree 8) / "
+                  "near-square 2D grid / Barabasi-Albert m=4 round-robin, U[0.5,1.5] weights, seed 1412")
+SERVE_WORKLOAD = ("requests drawn uniformly from {P} graphs with log n ~ Normal truncated to "
+                  "[ln 1e3, ln 2e6] (families and weights as the batch), Poisson arrivals")
+
+
+def _pool_workers():
+    return max(1, min(16, os.cpu_count() or 1))
+
+
+def run_batch(args, stream, flush):
+    """Batched form (many graphs per launch): setup + solve of the whole batch
+    per step; FP32 sweep form against the batched and the plain FP64 forms."""
+    import torch
+    from paper_1412_0565_gb300 import cmg, inputs
+    t0 = time.perf_counter()
+    graphs = inputs.batch_graphs(args.batch_graphs, workers=_pool_workers())
+    rp, col, w, offs = inputs.concat_csr(graphs)
+    gen_s = time.perf_counter() - t0
+    G, N, nnz = len(graphs), len(rp) - 1, int(rp[-1])
+    sid = stream.cuda_stream
+    drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
+    u = torch.empty(N, dtype=torch.float64, device="cuda")
+
+    def solve_steps(prec, K, shapes=None, replay=None, timing=0):
+        kw = dict(seed=1412, precision=prec, timing=timing)
+        if replay is not None:
+            kw["schedule"] = "replay"
+        step_ms, setup_ms, out = [], [], None
+        for k in range(K):
+            flush.zero_()
+            e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _e in range(3))
+            e0.record(stream)
+            b = cmg.Batch(offs, drp, dcol, dw, stream=sid, **kw)
+            if shapes:
+                for lvl, sh in enumerate(shapes):
+                    b.set_shape(lvl, *sh)
+            if replay is not None:
+                b.set_replay(replay)
+            em.record(stream)
+            _u, lam, _res, sts = b.fiedler(u_out=u, stream=sid)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            setup_ms.append(e0.elapsed_time(em))
+            out = (b, lam, sts)
+            if k + 1 < K:
+                b.close()
+        return step_ms, setup_ms, out
+
+    def tuned_shapes(prec):
+        b = cmg.Batch(offs, drp, dcol, dw, stream=sid, seed=1412, precision=prec)
+        b.autotune(stream=sid)
+        sh = [b.shape(lvl) for lvl in range(b.union_levels)]
+        b.close()
+        return sh
+
+    res = {"workload": BATCH_WORKLOAD, "graphs": G, "n_total": N, "nnz_total": nnz,
+           "generate_s": round(gen_s, 2),
+           "l2": "union CSR (1.7 GB) larger than L2; 256 MB buffer written between steps"}
+    for prec, K in (("fp32", args.batch_steps), ("fp64", 1)):
+        shapes = tuned_shapes(prec)
+        step_ms, setup_ms, (b, lam, sts) = solve_steps(prec, K, shapes)
+        st = [b.stats(q) for q in range(G)]
+        if prec == "fp64":
+            sweeps64 = [s_["sweeps"] for s_ in st]
+            lam64, u64 = lam.copy(), u.cpu().numpy()
+        else:
+            lam32_tol, u32_tol = lam.copy(), u.cpu().numpy()
+        b.close()
+        tot = sum(step_ms)
+        k0 = np.array([s_["sweeps"][0] for s_ in st])
+        visits = sum(s_["sweeps"][j] * (s_["n"][j] + s_["nnz"][j]) for s_ in st for j in range(s_["levels"]))
+        res[prec] = {"value": G * K / (tot / 1e3), "unit": "solves/s", "steps": K,
+                     "ms_per_step": tot / K, "setup_ms": statistics.median(setup_ms),
+                     "solve_ms": statistics.median(a - b_ for a, b_ in zip(step_ms, setup_ms)),
+                     "warn_maxiter": int((sts != 0).sum()), "shapes": shapes,
+                     "level0_sweeps": {"mean": float(k0.mean()), "max": int(k0.max())},
+                     "row_and_entry_visits": int(visits)}
+        if prec == "fp32":
+            # per-level device times (launches issued one by one) and the
+            # level-0 launch against HBM bandwidth
+            _, _, (bt, _, _) = solve_steps(prec, 1, shapes, timing=1)
+            lms = bt.level_ms()
+            stt = [bt.stats(q) for q in range(G)]
+            by0 = sum(s_["sweeps"][0] * (8 * s_["nnz"][0] + 12 * s_["n"][0]) for s_ in stt)
+            bt.close()
+            res[prec]["level_ms"] = [round(x, 2) for x in lms]
+            res[prec]["level0_launch"] = {"ms": lms[0], "algorithmic_bytes": by0,
+                                          "achieved_gbs": by0 / (lms[0] * 1e-3) / 1e9}
+    # precision alone: FP32 sweeps with the FP64 run's per-graph sweep counts
+    _, _, (b, lam32, _) = solve_steps("fp32", 1, None, replay=sweeps64)
+    u32 = u.cpu().numpy()
+    b.close()
+
+    def compare(lam_a, u_a):
+        rel = np.abs(lam_a - lam64) / np.abs(lam64)
+        ang = np.empty(G)
+        for q in range(G):
+            a_, c_ = u_a[offs[q]:offs[q + 1]], u64[offs[q]:offs[q + 1]]
+            cq = abs(float(np.dot(a_, c_))) / (np.linalg.norm(a_) * np.linalg.norm(c_))
+            ang[q] = np.arccos(min(1.0, cq))
+        return {"lambda2_rel_max": float(rel.max()), "lambda2_rel_p99": float(np.percentile(rel, 99)),
+                "angle_max": float(ang.max()), "angle_p99": float(np.percentile(ang, 99)),
+                "graphs_within_1e-6_and_1e-4": int(((rel <= 1e-6) & (ang <= 1e-4)).sum())}
+
+    res["fp32_vs_fp64_replay"] = compare(lam32, u32)
+    res["fp32_vs_fp64_replay"]["note"] = "FP32 sweeps with the FP64 run's per-graph, per-level sweep counts"
+    res["fp32_vs_fp64_tolerance_mode"] = compare(lam32_tol, u32_tol)
+    # the plain FP64 form: one graph at a time through cmg_setup / cmg_fiedler
+    idx = list(range(0, G, max(1, G // args.batch_plain_sample)))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for q in idx:
+        with cmg.Hierarchy(*graphs[q], seed=1412, stream=sid) as h:
+            h.fiedler(stream=sid)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    res["plain_fp64_single_graph"] = {"value": len(idx) / dt, "unit": "solves/s",
+                                      "sample": f"{len(idx)} graphs of the batch, host inputs, one at a time"}
+    res["fp32_batched_over_plain_fp64"] = res["fp32"]["value"] / res["plain_fp64_single_graph"]["value"]
+    return res
+
+
+def run_serving(args):
+    """Request loop: closed-loop saturation, then Poisson arrivals at 0.8 of
+    it; FP32 server (batching, resident hierarchies) and plain FP64 server
+    (no batching) on the same request trace."""
+    from paper_1412_0565_gb300 import cmg, inputs
+    graphs = inputs.serving_graphs(args.serve_graphs, workers=_pool_workers())
+    rng = np.random.default_rng(1412)
+    trace = rng.integers(0, len(graphs), size=args.serve_requests)
+    out = {"workload": SERVE_WORKLOAD.format(P=len(graphs)), "requests": int(len(trace)),
+           "distinct_graphs": len(graphs), "n_max": int(max(len(g[0]) - 1 for g in graphs)),
+           "n_median": int(np.median([len(g[0]) - 1 for g in graphs]))}
+    lam_by = {}
+    for name, cfg, prec in (("fp32", dict(workers=4, max_batch=256, batch_max_n=50000), "fp32"),
+                            ("fp64_plain", dict(workers=4, max_batch=1), "fp64")):
+        def run(rate):
+            with cmg.Server(seed=1412, precision=prec, **cfg) as srv:
+                ids = [srv.add_graph(*g) for g in graphs]
+                t0 = time.perf_counter()
+                tickets = []
+                if rate is None:
+                    tickets = [srv.submit(ids[k], want_vector=False) for k in trace]
+                else:
+                    arr = np.cumsum(np.random.default_rng(7).exponential(1.0 / rate, size=len(trace)))
+                    for k, ta in zip(trace, arr):
+                        d = t0 + ta - time.perf_counter()
+                        if d > 0:
+                            time.sleep(d)
+                        tickets.append(srv.submit(ids[k], want_vector=False))
+                rs = [srv.wait(t)[1] for t in tickets]
+                dt = time.perf_counter() - t0
+                return rs, dt, srv.stats()
+
+        rs, dt, st = run(None)
+        sat = len(trace) / dt
+        rs2, dt2, st2 = run(0.8 * sat)
+        lat = np.array([r["latency_ms"] for r in rs2])
+        lam_by[name] = np.array([r["lambda2"] for r in rs2])
+        out[name] = {"saturation_solves_s": sat, "rho": 0.8, "offered_rate": 0.8 * sat,
+                     "achieved_solves_s": len(trace) / dt2,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "warm_fraction": float(np.mean([r["warm"] for r in rs2])),
+                     "batched_fraction": float(np.mean([r["batch_size"] > 1 for r in rs2])),
+                     "jobs": {k: st2[k] for k in ("single_jobs", "batch_jobs", "warm_jobs", "evictions")},
+                     "peak_device_bytes": st2["peak_bytes"]}
+    rel = np.abs(lam_by["fp32"] - lam_by["fp64_plain"]) / np.abs(lam_by["fp64_plain"])
+    out["fp32_vs_fp64_lambda2_rel"] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
+                                       "note": "tolerance mode (sweep counts may differ)"}
+    return out
 
 
 def main():
@@ -358,6 +541,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--batch-graphs", type=int, default=4096)
+    ap.add_argument("--batch-steps", type=int, default=2)
+    ap.add_argument("--batch-plain-sample", type=int, default=32)
+    ap.add_argument("--serve-graphs", type=int, default=48)
+    ap.add_argument("--serve-requests", type=int, default=160)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -57,7 +57,8 @@ typedef enum cmg_status {
     CMG_ERR_DEVICE_TIMEOUT = -9,   /* a bounded device-side wait gave up                  */
     CMG_ERR_BAD_CSR = -10,         /* row_ptr not monotone, column out of range,
                                       columns not strictly ascending                      */
-    CMG_ERR_TOO_LARGE = -11        /* nnz >= 2^31 or a size beyond a stated limit         */
+    CMG_ERR_TOO_LARGE = -11,       /* nnz >= 2^31 or a size beyond a stated limit         */
+    CMG_ERR_TIMEOUT = -12          /* a host-side wait with a time limit gave up          */
 } cmg_status_t;
 
 enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 };
@@ -333,6 +334,10 @@ cmg_status_t cmg_server_submit(cmg_server_t s, int64_t graph_id, double *u_out, 
 /* Blocks until the request completes; fills *out (nullable) and returns the
  * request's status.  A ticket can be waited for once. */
 cmg_status_t cmg_server_wait(cmg_server_t s, int64_t ticket, cmg_request_t *out);
+/* cmg_server_wait that gives up after timeout_ms milliseconds with
+ * CMG_ERR_TIMEOUT (the request stays queued and can be waited for again). */
+cmg_status_t cmg_server_wait_for(cmg_server_t s, int64_t ticket, int64_t timeout_ms,
+                                 cmg_request_t *out);
 cmg_status_t cmg_server_get_stats(cmg_server_t s, cmg_server_stats_t *out);
 /* Finishes every queued request, stops the workers, frees the hierarchies. */
 cmg_status_t cmg_server_destroy(cmg_server_t s);

@@ -27,7 +27,7 @@ STATUS = {
     0: "OK", 1: "WARN_MAXITER", -1: "ERR_INVALID_ARG", -2: "ERR_NOT_SYMMETRIC",
     -3: "ERR_SELF_LOOP", -4: "ERR_BAD_WEIGHT", -5: "ERR_ISOLATED_VERTEX", -6: "ERR_TOO_SMALL",
     -7: "ERR_OOM", -8: "ERR_CUDA", -9: "ERR_DEVICE_TIMEOUT", -10: "ERR_BAD_CSR",
-    -11: "ERR_TOO_LARGE",
+    -11: "ERR_TOO_LARGE", -12: "ERR_TIMEOUT",
 }
 
 # every symbol include/cmg.h declares
@@ -41,7 +41,8 @@ EXPORTS = [
     "cmg_batch_get_aggregates", "cmg_batch_get_level_csr", "cmg_batch_set_replay",
     "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
     "cmg_batch_free", "cmg_server_config_default", "cmg_server_create", "cmg_server_add_graph",
-    "cmg_server_submit", "cmg_server_wait", "cmg_server_get_stats", "cmg_server_destroy",
+    "cmg_server_submit", "cmg_server_wait", "cmg_server_wait_for", "cmg_server_get_stats",
+    "cmg_server_destroy",
 ]
 
 NOALLOC_MAX_N = 262144
@@ -171,6 +172,7 @@ def load(build_if_stale: bool = True):
             "cmg_server_add_graph": (I32, [V, I64, V, V, V, P(I64)]),
             "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
             "cmg_server_wait": (I32, [V, I64, P(Request)]),
+            "cmg_server_wait_for": (I32, [V, I64, I64, P(Request)]),
             "cmg_server_get_stats": (I32, [V, P(ServerStats)]),
             "cmg_server_destroy": (I32, [V]),
         }
@@ -517,10 +519,16 @@ class Server:
         self._outs[t.value] = u
         return t.value
 
-    def wait(self, ticket: int):
-        """Returns (u or None, request dict); raises on a failed request."""
+    def wait(self, ticket: int, timeout_s: float | None = None):
+        """Returns (u or None, request dict); raises on a failed request (and
+        with ERR_TIMEOUT when timeout_s passes first)."""
         r = Request()
-        st = load().cmg_server_wait(self._s, ticket, C.byref(r))
+        if timeout_s is None:
+            st = load().cmg_server_wait(self._s, ticket, C.byref(r))
+        else:
+            st = load().cmg_server_wait_for(self._s, ticket, int(timeout_s * 1000), C.byref(r))
+            if st == -12:
+                raise CmgError(st, "server_wait")
         u = self._outs.pop(ticket, None)
         _check(st, "server_wait")
         return u, r.as_dict()

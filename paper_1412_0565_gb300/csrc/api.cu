@@ -383,6 +383,7 @@ const char *cmg_status_string(cmg_status_t s) {
         case CMG_ERR_DEVICE_TIMEOUT: return "device-side wait timed out";
         case CMG_ERR_BAD_CSR: return "malformed CSR (row pointers, column range or order)";
         case CMG_ERR_TOO_LARGE: return "graph too large";
+        case CMG_ERR_TIMEOUT: return "host-side wait timed out";
     }
     return "unknown status";
 }

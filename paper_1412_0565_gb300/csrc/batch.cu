@@ -102,12 +102,30 @@ constexpr int kOffInt = kOffDred + 32 * 4 * (int)sizeof(double);
 constexpr int kBatchMaxThreads = 512;
 static_assert(kOffInt + 64 <= kGroupHeader, "group header too small");
 
+// Sweep layout of a level, per graph (built at setup): rows renumbered by
+// decreasing degree (stable); the rows with more than kHeavy entries come
+// first and keep CSR form ("heavy" rows), the others form slices of 32 rows
+// whose entries are interleaved -- entry k of the slice's row l sits at
+// slice_offset + 32 k + l, shorter rows padded with weight 0 -- so a warp
+// reads a slice with coalesced loads that do not depend on each other.
+// Columns are renumbered local ids (16-bit when every graph of the level
+// has at most 65536 vertices).  meta of a graph: h + 1 heavy row pointers,
+// then nsl + 1 slice offsets (entry offsets local to the graph).
+constexpr int kHeavy = 32;
+
 struct BatchPiArgs {
     int level;
-    const int *rp;
+    const int *rp;        // the level's CSR (original numbering): finalisation
     const int *col;
     const double *w;
-    const float *w32;
+    const int *perm;      // new union position -> original union vertex
+    const int *inv;       // original union vertex -> new union position
+    const int *heavy;     // [G] heavy rows per graph
+    const int *eoff;      // [G] first layout entry of each graph
+    const int *moff;      // [G] first meta word of each graph
+    const int *meta;
+    const void *bcol;     // layout columns (uint16 or int32)
+    const void *bw;       // layout weights (T)
     const int *voff;      // [G+1] union offsets of the graphs on this level
     const double *gsh;    // [G]   Gershgorin shift per graph
     const int *list;      // graphs solved on this level (largest first)
@@ -122,7 +140,7 @@ struct BatchPiArgs {
     double *gdscr;        // double[n_level] g - d_i of those graphs (FP64 form)
     int tg;               // threads per graph
     int smem_group;       // shared bytes per group, header included
-    int stage;            // copy the CSR to shared memory when it fits
+    int stage;            // copy the layout to shared memory when it fits
     int fixed;            // schedule FIXED: k_fixed sweeps below the coarsest level
     int k_fixed;
     const int *replay;    // schedule REPLAY: [G][CMG_MAX_LEVELS] sweep counts
@@ -190,41 +208,15 @@ __device__ __forceinline__ bool sign_better(double v, int i, double bv, int bi) 
     return v > bv || (v == bv && i < bi);
 }
 
-// Row sum of one sweep with G lanes per row: FP32 edge form sum w (x_i - x_j),
-// FP64 degree form sum w x_j (four independent accumulators).
-template <typename T, int G>
-__device__ __forceinline__ T row_sweep(const int *R, const int *C, const T *W, const T *x, int cshift,
-                                       int i, int rl, T xi) {
-    constexpr bool fp64 = sizeof(T) == 8;
-    T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-    int e = R[i] + rl;
-    const int e1 = R[i + 1];
-    for (; e + 3 * G < e1; e += 4 * G) {
-        const int c0 = C[e] - cshift, c1 = C[e + G] - cshift, c2 = C[e + 2 * G] - cshift,
-                  c3 = C[e + 3 * G] - cshift;
-        const T w0 = W[e], w1 = W[e + G], w2 = W[e + 2 * G], w3 = W[e + 3 * G];
-        const T x0 = x[c0], x1 = x[c1], x2 = x[c2], x3 = x[c3];
-        if (fp64) {
-            a0 = fma(w0, x0, a0);
-            a1 = fma(w1, x1, a1);
-            a2 = fma(w2, x2, a2);
-            a3 = fma(w3, x3, a3);
-        } else {
-            a0 += w0 * (xi - x0);
-            a1 += w1 * (xi - x1);
-            a2 += w2 * (xi - x2);
-            a3 += w3 * (xi - x3);
-        }
-    }
-    for (; e < e1; e += G) {
-        const T xv = x[C[e] - cshift];
-        if (fp64) a0 = fma(W[e], xv, a0);
-        else a0 += W[e] * (xi - xv);
-    }
-    return (a0 + a1) + (a2 + a3);
+// One sweep's contribution of row i: FP32 edge form sum w (x_i - x_j), FP64
+// degree form sum w x_j.
+template <typename T>
+__device__ __forceinline__ T edge_term(T acc, T w, T xi, T xj) {
+    if (sizeof(T) == 8) return fma(w, xj, acc);
+    return acc + w * (xi - xj);
 }
 
-template <typename T, int G>
+template <typename T, typename IDX, int G>
 __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp64 = sizeof(T) == 8;
@@ -240,8 +232,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
     int *s_int = reinterpret_cast<int *>(gbase + kOffInt);
     unsigned char *data = gbase + kGroupHeader;
     const long long data_bytes = (long long)a.smem_group - kGroupHeader;
-    const T *wsrc = fp64 ? (const T *)a.w : (const T *)a.w32;
     const int rg = gt / G, rl = gt & (G - 1), ngr = tg / G;
+    constexpr int kRpw = 32 / G;   // heavy rows per warp pass
 
     for (;;) {
         // ---- next graph from the queue
@@ -258,7 +250,11 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
         if (k >= a.count) break;
         const int q = a.list[k];
         const int v0 = a.voff[q], n = a.voff[q + 1] - v0;
-        const int e0 = a.rp[v0], nnz = a.rp[v0 + n] - e0;
+        const int h = a.heavy[q];
+        const int nsl = (n - h + 31) >> 5;
+        const int *gmeta = a.meta + a.moff[q];
+        const int nm = h + nsl + 2;
+        const int ne = gmeta[nm - 1];
         const double gsh = a.gsh[q];
         const bool coarsest = a.level == a.J[q];
         int mode = 0, kfix = 0;   // 0: until cos >= 1 - tol, 1: exactly kfix sweeps
@@ -275,14 +271,14 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
         const int maxs = coarsest ? a.max_sweeps_coarsest : a.max_sweeps;
         const bool gauss = coarsest || a.force_k >= 0;
 
-        // ---- placement: vectors (and the CSR) in shared memory when they fit
+        // ---- placement: iterates (and the layout) in shared memory when they fit
         const long long vbytes = (long long)n * (2 * (long long)sizeof(T) + (fp64 ? 8 : 0));
-        const long long cbytes = 4ll * (n + 1) + (long long)nnz * (4 + (long long)sizeof(T));
+        const long long cbytes = (long long)ne * (long long)(sizeof(T) + sizeof(IDX)) + 4ll * nm + 16;
         T *X0, *X1;
         double *GD = nullptr;
-        const int *R, *C;
+        const int *M;
+        const IDX *C;
         const T *W;
-        int cshift;
         if (a.stage && vbytes + cbytes <= data_bytes) {
             X0 = reinterpret_cast<T *>(data);
             X1 = X0 + n;
@@ -292,17 +288,18 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
                 p += 8ll * n;
             }
             T *sW = reinterpret_cast<T *>(p);
-            int *sR = reinterpret_cast<int *>(sW + nnz);
-            int *sC = sR + n + 1;
-            for (int i = gt; i <= n; i += tg) sR[i] = a.rp[v0 + i] - e0;
-            for (int e = gt; e < nnz; e += tg) {
-                sC[e] = a.col[e0 + e] - v0;
-                sW[e] = wsrc[e0 + e];
+            int *sM = reinterpret_cast<int *>(sW + ne);
+            IDX *sC = reinterpret_cast<IDX *>(sM + nm);
+            const T *gw = reinterpret_cast<const T *>(a.bw) + a.eoff[q];
+            const IDX *gc = reinterpret_cast<const IDX *>(a.bcol) + a.eoff[q];
+            for (int e = gt; e < ne; e += tg) {
+                sW[e] = gw[e];
+                sC[e] = gc[e];
             }
-            R = sR;
+            for (int m = gt; m < nm; m += tg) sM[m] = gmeta[m];
+            M = sM;
             C = sC;
             W = sW;
-            cshift = 0;
         } else {
             if (vbytes <= data_bytes) {
                 X0 = reinterpret_cast<T *>(data);
@@ -313,14 +310,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
                 X1 = X0 + n;
                 if (fp64) GD = a.gdscr + v0;
             }
-            R = a.rp + v0;
-            C = a.col;
-            W = wsrc;
-            cshift = v0;
+            M = gmeta;
+            C = reinterpret_cast<const IDX *>(a.bcol) + a.eoff[q];
+            W = reinterpret_cast<const T *>(a.bw) + a.eoff[q];
         }
+        const int *SO = M + h + 1;   // slice offsets
         gbar(bid, tg);
 
-        // ---- start vector: Gaussian (Alg. 1 Step 2) or I^T y (Alg. 1 Step 3)
+        // ---- start vector (renumbered rows): Gaussian (Alg. 1 Step 2) or
+        // I^T y (Alg. 1 Step 3) of the original vertex
         Part p0;
         p0.A = ff_zero();
         p0.B = ff_zero();
@@ -328,12 +326,19 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
         {
             const T *ucT = reinterpret_cast<const T *>(a.uc);
             for (int i = gt; i < n; i += tg) {
-                const double xv = gauss ? gaussian_entry(a.seed, i) : (double)ucT[a.agg[v0 + i]];
+                const int old = a.perm[v0 + i];
+                const double xv = gauss ? gaussian_entry(a.seed, old - v0) : (double)ucT[a.agg[old]];
                 const T xt = (T)xv;
                 X0[i] = xt;
                 if (fp64) {
                     double d = 0.0;
-                    for (int e = R[i], e1 = R[i + 1]; e < e1; e++) d += (double)W[e];
+                    if (i < h) {
+                        for (int e = M[i], e1 = M[i + 1]; e < e1; e++) d += (double)W[e];
+                    } else {
+                        const int sl = (i - h) >> 5, l = (i - h) & 31;
+                        const int so = SO[sl], wd = (SO[sl + 1] - so) >> 5;
+                        for (int kk = 0; kk < wd; kk++) d += (double)W[so + 32 * kk + l];
+                    }
                     GD[i] = gsh - d;
                 }
                 const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
@@ -370,24 +375,49 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             const T gm = (T)gsh * mT;
             Acc<T> acc;
             acc.reset();
-            for (int base = rg;; base += ngr) {
-                if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
-                const int i = base;
+            auto finish_row = [&](int i, T xi, T ac) {
+                T yv;
+                if (fp64) yv = (T)((fma((double)GD[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
+                else yv = ((T)gsh * (xi - mT) - ac) * sig;
+                y[i] = yv;
+                acc.add(yv, xi);
+            };
+            // heavy rows: G lanes per row
+            for (int base = wg * kRpw;; base += nwg * kRpw) {
+                if (base >= h) break;
+                const int i = base + lane / G;
                 T ac = (T)0, xi = (T)0;
-                if (i < n) {
+                if (i < h) {
                     xi = x[i];
-                    ac = row_sweep<T, G>(R, C, W, x, cshift, i, rl, xi);
+                    for (int f = M[i] + rl, f1 = M[i + 1]; f < f1; f += G)
+                        ac = edge_term<T>(ac, W[f], xi, x[C[f]]);
                 }
                 ac = group_sum<G>(ac);
-                if (i < n && rl == 0) {
-                    T yv;
-                    if (fp64) yv = (T)((fma((double)GD[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
-                    else yv = ((T)gsh * (xi - mT) - ac) * sig;
-                    y[i] = yv;
-                    acc.add(yv, xi);
-                }
+                if (i < h && rl == 0) finish_row(i, xi, ac);
             }
-            const Part P = gsum_part<G>(acc.get(), s_part + 32 * ((s + 1) & 1), lane, wg, nwg, bid, tg);
+            // light rows: one warp per slice of 32 rows, coalesced entries
+            for (int sl = wg; sl < nsl; sl += nwg) {
+                const int i = h + 32 * sl + lane;
+                const int so = SO[sl] + lane, wd = (SO[sl + 1] - SO[sl]) >> 5;
+                const T xi = (i < n) ? x[i] : (T)0;
+                T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+                int kk = 0;
+                for (; kk + 3 < wd; kk += 4) {
+                    const int f = so + 32 * kk;
+                    const int c0 = C[f], c1 = C[f + 32], c2 = C[f + 64], c3 = C[f + 96];
+                    const T w0 = W[f], w1 = W[f + 32], w2 = W[f + 64], w3 = W[f + 96];
+                    a0 = edge_term<T>(a0, w0, xi, x[c0]);
+                    a1 = edge_term<T>(a1, w1, xi, x[c1]);
+                    a2 = edge_term<T>(a2, w2, xi, x[c2]);
+                    a3 = edge_term<T>(a3, w3, xi, x[c3]);
+                }
+                for (; kk < wd; kk++) {
+                    const int f = so + 32 * kk;
+                    a0 = edge_term<T>(a0, W[f], xi, x[C[f]]);
+                }
+                if (i < n) finish_row(i, xi, (a0 + a1) + (a2 + a3));
+            }
+            const Part P = gsum_part<1>(acc.get(), s_part + 32 * ((s + 1) & 1), lane, wg, nwg, bid, tg);
             const ff mu1 = ff_mul(P.A, inv_n);
             const ff ss1 = ff_add_f(P.B, -nf * mu1.hi * mu1.hi);
             const ff cs = ff_add_f(P.C, -nf * mu1.hi * mu.hi);
@@ -411,7 +441,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             e = -(int)floorf(0.5f * log2f(fmaxf(ss.hi, 1e-37f)) + 0.5f);
         }
 
-        // ---- result of this level
+        // ---- result of this level, back in the original numbering
         const T *Yr = cur ? X1 : X0;
         const T *Yp = cur ? X0 : X1;
         const double r_mu = to_d(mu), r_ss = to_d(ss);
@@ -424,29 +454,30 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             r_cos = den > 0.0 ? to_d(cs_last) / den : 1.0;
         }
         if (a.level > 0) {
-            T *uo = reinterpret_cast<T *>(a.uo) + v0;
-            for (int i = gt; i < n; i += tg) uo[i] = (T)(((double)Yr[i] - r_mu) * r_inv);
+            T *uo = reinterpret_cast<T *>(a.uo);
+            for (int i = gt; i < n; i += tg) uo[a.perm[v0 + i]] = (T)(((double)Yr[i] - r_mu) * r_inv);
         } else {
             double *u = a.uf + v0;
             if (!fp64 && s > 0 && !zero_hit) {
-                // FP64 recomputation of the last sweep from the previous (FP32) iterate
+                // FP64 recomputation of the last sweep from the previous (FP32)
+                // iterate, over the original CSR
                 const double mp = to_d(mu_p), sp = to_d(ss_p);
                 const double ip = sp > 0.0 ? 1.0 / sqrt(sp) : 0.0;
                 double p2[2] = {0.0, 0.0};
                 for (int base = rg;; base += ngr) {
                     if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
                     const int i = base;
-                    double acc = 0.0, xi = 0.0;
+                    double accd = 0.0, xi = 0.0;
                     if (i < n) {
-                        xi = ((double)Yp[i] - mp) * ip;
+                        xi = ((double)Yp[a.inv[v0 + i] - v0] - mp) * ip;
                         for (int f = a.rp[v0 + i] + rl, f1 = a.rp[v0 + i + 1]; f < f1; f += G) {
-                            const double xj = ((double)Yp[a.col[f] - v0] - mp) * ip;
-                            acc += a.w[f] * (xi - xj);
+                            const double xj = ((double)Yp[a.inv[a.col[f]] - v0] - mp) * ip;
+                            accd += a.w[f] * (xi - xj);
                         }
                     }
-                    acc = group_sum<G>(acc);
+                    accd = group_sum<G>(accd);
                     if (i < n && rl == 0) {
-                        const double yv = gsh * xi - acc;
+                        const double yv = gsh * xi - accd;
                         u[i] = yv;
                         p2[0] += yv;
                         p2[1] += yv * yv;
@@ -458,7 +489,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
                 const double i2 = s2 > 0.0 ? 1.0 / sqrt(s2) : 0.0;
                 for (int i = gt; i < n; i += tg) u[i] = (u[i] - m2) * i2;
             } else {
-                for (int i = gt; i < n; i += tg) u[i] = ((double)Yr[i] - r_mu) * r_inv;
+                for (int i = gt; i < n; i += tg) u[a.perm[v0 + i] - v0] = ((double)Yr[i] - r_mu) * r_inv;
             }
             gbar(bid, tg);
             // canonical sign: largest |u_i| (lowest i on ties) made positive
@@ -522,17 +553,17 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             for (int base = rg;; base += ngr) {
                 if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
                 const int i = base;
-                double acc = 0.0, ui = 0.0;
+                double accd = 0.0, ui = 0.0;
                 if (i < n) {
                     ui = u[i];
                     for (int f = a.rp[v0 + i] + rl, f1 = a.rp[v0 + i + 1]; f < f1; f += G) {
                         const double d = ui - u[a.col[f] - v0];
-                        acc += a.w[f] * d * d;
+                        accd += a.w[f] * d * d;
                     }
                 }
-                acc = group_sum<G>(acc);
+                accd = group_sum<G>(accd);
                 if (i < n && rl == 0) {
-                    p2[0] += acc;
+                    p2[0] += accd;
                     p2[1] += ui * ui;
                 }
             }
@@ -543,15 +574,15 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             for (int base = rg;; base += ngr) {
                 if (__shfl_sync(0xffffffffu, base, 0) >= n) break;
                 const int i = base;
-                double acc = 0.0, ui = 0.0;
+                double accd = 0.0, ui = 0.0;
                 if (i < n) {
                     ui = u[i];
                     for (int f = a.rp[v0 + i] + rl, f1 = a.rp[v0 + i + 1]; f < f1; f += G)
-                        acc += a.w[f] * (ui - u[a.col[f] - v0]);
+                        accd += a.w[f] * (ui - u[a.col[f] - v0]);
                 }
-                acc = group_sum<G>(acc);
+                accd = group_sum<G>(accd);
                 if (i < n && rl == 0) {
-                    const double rr = acc - lam * ui;
+                    const double rr = accd - lam * ui;
                     p1[0] += rr * rr;
                 }
             }
@@ -573,21 +604,172 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
 
 typedef void (*BatchKernel)(BatchPiArgs);
 
-template <typename T>
-static BatchKernel batch_kernel_t(int G) {
+template <typename T, typename IDX>
+static BatchKernel batch_kernel_ti(int G) {
     switch (G) {
-        case 1: return k_batch_pi<T, 1>;
-        case 2: return k_batch_pi<T, 2>;
-        case 4: return k_batch_pi<T, 4>;
-        case 8: return k_batch_pi<T, 8>;
-        case 16: return k_batch_pi<T, 16>;
-        case 32: return k_batch_pi<T, 32>;
+        case 1: return k_batch_pi<T, IDX, 1>;
+        case 2: return k_batch_pi<T, IDX, 2>;
+        case 4: return k_batch_pi<T, IDX, 4>;
+        case 8: return k_batch_pi<T, IDX, 8>;
+        case 16: return k_batch_pi<T, IDX, 16>;
+        case 32: return k_batch_pi<T, IDX, 32>;
         default: return nullptr;
     }
 }
 
-static BatchKernel batch_kernel(int fp32, int G) {
-    return fp32 ? batch_kernel_t<float>(G) : batch_kernel_t<double>(G);
+static BatchKernel batch_kernel(int fp32, int col16, int G) {
+    if (fp32) return col16 ? batch_kernel_ti<float, uint16_t>(G) : batch_kernel_ti<float, int>(G);
+    return col16 ? batch_kernel_ti<double, uint16_t>(G) : batch_kernel_ti<double, int>(G);
+}
+
+// ------------------------------------------------------------------ layout kernels
+// keys (graph, decreasing degree) of every union vertex, for a stable sort
+__global__ void k_layout_keys(int n, int G, const int *__restrict__ voff, const int *__restrict__ rp,
+                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (voff[mid] <= v) lo = mid;
+            else hi = mid - 1;
+        }
+        const uint32_t deg = (uint32_t)(rp[v + 1] - rp[v]);
+        keys[v] = ((uint64_t)lo << 32) | (uint64_t)(0xffffffffu - deg);
+        vals[v] = (uint32_t)v;
+    }
+}
+
+__global__ void k_layout_inv(int n, const uint32_t *__restrict__ perm, int *__restrict__ inv) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
+        inv[perm[p]] = p;
+}
+
+__device__ __forceinline__ int perm_deg(const int *rp, const uint32_t *perm, int p) {
+    const int v = (int)perm[p];
+    return rp[v + 1] - rp[v];
+}
+
+// Per graph (one warp): heavy rows h, layout entries and meta words.
+__global__ void k_layout_count(int G, const int *__restrict__ voff, const int *__restrict__ rp,
+                               const uint32_t *__restrict__ perm, int *__restrict__ heavy,
+                               int *__restrict__ ecnt, int *__restrict__ mcnt) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < G; q += warps) {
+        const int v0 = voff[q], n = voff[q + 1] - v0;
+        int h = 0, he = 0;
+        for (int p = lane; p < n; p += 32) {
+            const int d = perm_deg(rp, perm, v0 + p);
+            if (d > kHeavy) {
+                h++;
+                he += d;
+            }
+        }
+        h = warp_sum_int(h);
+        he = warp_sum_int(he);
+        const int nsl = (n - h + 31) >> 5;
+        int se = 0;
+        for (int sl = lane; sl < nsl; sl += 32) se += 32 * perm_deg(rp, perm, v0 + h + 32 * sl);
+        se = warp_sum_int(se);
+        if (lane == 0) {
+            heavy[q] = h;
+            ecnt[q] = he + se;
+            mcnt[q] = h + nsl + 2;
+        }
+    }
+}
+
+// Per graph (one warp): heavy row pointers, then slice offsets.
+__global__ void k_layout_meta(int G, const int *__restrict__ voff, const int *__restrict__ rp,
+                              const uint32_t *__restrict__ perm, const int *__restrict__ heavy,
+                              const int *__restrict__ moff, int *__restrict__ meta) {
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < G; q += warps) {
+        const int v0 = voff[q], n = voff[q + 1] - v0, h = heavy[q];
+        const int nsl = (n - h + 31) >> 5;
+        int *m = meta + moff[q];
+        const int items = h + nsl;   // heavy rows, then slices
+        int run = 0;
+        for (int t0 = 0; t0 < items; t0 += 32) {
+            const int t = t0 + lane;
+            int len = 0;
+            if (t < h) len = perm_deg(rp, perm, v0 + t);
+            else if (t < items) len = 32 * perm_deg(rp, perm, v0 + h + 32 * (t - h));
+            int x = len;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            const int excl = run + x - len;
+            // heavy row t starts at excl (meta word t); slice t-h starts at excl
+            // (meta word h + 1 + t - h)
+            if (t < h) m[t] = excl;
+            else if (t < items) m[t + 1] = excl;
+            run += __shfl_sync(0xffffffffu, x, 31);
+        }
+        if (lane == 0) {
+            // end of the heavy rows = start of the first slice
+            int he = 0;
+            for (int t = 0; t < h; t++) he += perm_deg(rp, perm, v0 + t);
+            m[h] = he;
+            m[h + 1 + nsl] = run;
+        }
+    }
+}
+
+// Entries of every renumbered row; the last slice's phantom rows (past n) and
+// short rows are padded with weight 0 and a valid column.
+template <typename T, typename IDX>
+__global__ void k_layout_fill(int n, int G, const int *__restrict__ voff, const int *__restrict__ rp,
+                              const int *__restrict__ col, const double *__restrict__ w,
+                              const uint32_t *__restrict__ perm, const int *__restrict__ inv,
+                              const int *__restrict__ heavy, const int *__restrict__ eoff,
+                              const int *__restrict__ moff, const int *__restrict__ meta,
+                              IDX *__restrict__ bcol, T *__restrict__ bw) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
+        int lo = 0, hi = G - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (voff[mid] <= p) lo = mid;
+            else hi = mid - 1;
+        }
+        const int q = lo, v0 = voff[q], ng = voff[q + 1] - v0, r = p - v0, h = heavy[q];
+        const int *m = meta + moff[q];
+        const int v = (int)perm[p];
+        const int e0 = rp[v], deg = rp[v + 1] - e0;
+        IDX *gc = bcol + eoff[q];
+        T *gw = bw + eoff[q];
+        if (r < h) {
+            const int d0 = m[r];
+            for (int j = 0; j < deg; j++) {
+                gc[d0 + j] = (IDX)(inv[col[e0 + j]] - v0);
+                gw[d0 + j] = (T)w[e0 + j];
+            }
+            continue;
+        }
+        const int sl = (r - h) >> 5, l = (r - h) & 31;
+        const int so = m[h + 1 + sl], wd = (m[h + 2 + sl] - so) >> 5;
+        for (int j = 0; j < wd; j++) {
+            const int d = so + 32 * j + l;
+            if (j < deg) {
+                gc[d] = (IDX)(inv[col[e0 + j]] - v0);
+                gw[d] = (T)w[e0 + j];
+            } else {
+                gc[d] = (IDX)r;
+                gw[d] = (T)0;
+            }
+        }
+        // the graph's last row also pads the phantom rows of its last slice
+        if (r == ng - 1) {
+            for (int l2 = l + 1; l2 < 32; l2++)
+                for (int j = 0; j < wd; j++) {
+                    gc[so + 32 * j + l2] = (IDX)0;
+                    gw[so + 32 * j + l2] = (T)0;
+                }
+        }
+    }
 }
 
 }  // namespace cmg
@@ -603,8 +785,15 @@ struct BLevel {
     int *rp = nullptr;
     int *col = nullptr;
     double *w = nullptr;
-    float *w32 = nullptr;
     int *agg = nullptr;          // onto the next union level
+    // sweep layout (rows renumbered by degree; heavy CSR rows + 32-row slices)
+    uint32_t *perm = nullptr;    // new union position -> original union vertex
+    int *inv = nullptr;
+    int *heavy = nullptr, *eoff = nullptr, *moff = nullptr, *meta = nullptr;
+    void *bcol = nullptr;        // uint16 (col16) or int32 local columns
+    void *bw = nullptr;          // sweep-precision weights
+    int col16 = 1;
+    std::vector<int> hecnt, hmcnt;   // per-graph layout entries and meta words
     int *voff = nullptr;         // device int[G+1]
     double *gsh = nullptr;       // device double[G]
     std::vector<int> hvoff;      // host copies
@@ -625,7 +814,14 @@ void free_blevel(BLevel &L, cudaStream_t s) {
     dev_free(L.rp, s);
     dev_free(L.col, s);
     dev_free(L.w, s);
-    dev_free(L.w32, s);
+    dev_free(L.perm, s);
+    dev_free(L.inv, s);
+    dev_free(L.heavy, s);
+    dev_free(L.eoff, s);
+    dev_free(L.moff, s);
+    dev_free(L.meta, s);
+    dev_free(L.bcol, s);
+    dev_free(L.bw, s);
     dev_free(L.agg, s);
     dev_free(L.voff, s);
     dev_free(L.gsh, s);
@@ -750,12 +946,11 @@ static cmg_status_t level_workspace(cmg_batch_s *b, int j, cudaStream_t s) {
             b->bytes += sizeof(double) * (size_t)L.n;
         }
     }
-    BatchKernel kern = batch_kernel(fp32, L.shape.lanes_per_row);
+    BatchKernel kern = batch_kernel(fp32, L.col16, L.shape.lanes_per_row);
     if (!kern) return CMG_ERR_INVALID_ARG;
     const int smem = L.smem_group * L.shape.graphs_per_cta;
     if (smem > di.max_smem_optin) return CMG_ERR_INVALID_ARG;
-    CMG_CUDA(cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  di.max_smem_optin));
+    CMG_TRY(allow_max_dynamic_smem((const void *)kern));
     return CMG_OK;
 }
 
@@ -764,7 +959,7 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     if (L.count == 0) return CMG_OK;
     const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
     const cmg_options_t &o = b->opts;
-    BatchKernel kern = batch_kernel(fp32, L.shape.lanes_per_row);
+    BatchKernel kern = batch_kernel(fp32, L.col16, L.shape.lanes_per_row);
     const int threads = threads_for_gpc(L.shape);
     const int smem = L.smem_group * L.shape.graphs_per_cta;
     int per_sm = 0;
@@ -779,7 +974,14 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     a.rp = L.rp;
     a.col = L.col;
     a.w = L.w;
-    a.w32 = L.w32;
+    a.perm = reinterpret_cast<const int *>(L.perm);
+    a.inv = L.inv;
+    a.heavy = L.heavy;
+    a.eoff = L.eoff;
+    a.moff = L.moff;
+    a.meta = L.meta;
+    a.bcol = L.bcol;
+    a.bw = L.bw;
     a.voff = L.voff;
     a.gsh = L.gsh;
     a.list = L.list;
@@ -820,6 +1022,78 @@ static cmg_status_t enqueue_solve(cmg_batch_s *b, int force_k, cudaStream_t s) {
     return CMG_OK;
 }
 
+// Sweep layout of union level j (see k_layout_*): stable sort of the rows by
+// (graph, decreasing degree), per-graph counts, offsets, then the entries.
+static cmg_status_t build_layout(cmg_batch_s *b, int j, cudaStream_t s, size_t *bytes) {
+    BLevel &L = b->lv[j];
+    const int G = b->G, N = L.n;
+    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+    int maxn = 0;
+    for (int q = 0; q < G; q++) maxn = std::max(maxn, L.hvoff[q + 1] - L.hvoff[q]);
+    L.col16 = maxn <= 65536 ? 1 : 0;
+    Scratch scr(s);
+    uint64_t *ka, *kb;
+    uint32_t *va, *vb;
+    int *cnt_n, *ecnt, *mcnt;
+    CMG_TRY(scr.get(&ka, (size_t)N));
+    CMG_TRY(scr.get(&kb, (size_t)N));
+    CMG_TRY(scr.get(&va, (size_t)N));
+    CMG_TRY(scr.get(&vb, (size_t)N));
+    CMG_TRY(scr.get(&cnt_n, 1));
+    CMG_TRY(scr.get(&ecnt, (size_t)G));
+    CMG_TRY(scr.get(&mcnt, (size_t)G));
+    CMG_CUDA(cudaMemcpyAsync(cnt_n, &L.n, sizeof(int), cudaMemcpyHostToDevice, s));
+    k_layout_keys<<<grid_for(N, 256), 256, 0, s>>>(N, G, L.voff, L.rp, ka, va);
+    CMG_TRY(launch_status());
+    CMG_TRY(radix_sort_pairs(&ka, &va, kb, vb, N, cnt_n, 32 + bits_for(G), scr, s));
+    CMG_TRY(dev_alloc_n(&L.perm, (size_t)N, s));
+    CMG_TRY(dev_alloc_n(&L.inv, (size_t)N, s));
+    CMG_CUDA(cudaMemcpyAsync(L.perm, va, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
+    k_layout_inv<<<grid_for(N, 256), 256, 0, s>>>(N, L.perm, L.inv);
+    CMG_TRY(launch_status());
+    CMG_TRY(dev_alloc_n(&L.heavy, (size_t)G, s));
+    CMG_TRY(dev_alloc_n(&L.eoff, (size_t)G + 1, s));
+    CMG_TRY(dev_alloc_n(&L.moff, (size_t)G + 1, s));
+    const int wblocks = grid_for((long long)G * 32, 256);
+    k_layout_count<<<wblocks, 256, 0, s>>>(G, L.voff, L.rp, L.perm, L.heavy, ecnt, mcnt);
+    CMG_TRY(launch_status());
+    CMG_TRY(exclusive_scan(ecnt, L.eoff, G, scr, s));
+    CMG_TRY(exclusive_scan(mcnt, L.moff, G, scr, s));
+    L.hecnt.resize(G);
+    L.hmcnt.resize(G);
+    int tot[2] = {0, 0};
+    CMG_CUDA(cudaMemcpyAsync(L.hecnt.data(), ecnt, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaMemcpyAsync(L.hmcnt.data(), mcnt, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaMemcpyAsync(&tot[0], L.eoff + G, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaMemcpyAsync(&tot[1], L.moff + G, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaStreamSynchronize(s));
+    long long te = 0, tm = 0;
+    for (int q = 0; q < G; q++) {
+        te += L.hecnt[q];
+        tm += L.hmcnt[q];
+    }
+    if (te != tot[0] || tm != tot[1] || te >= 2147483647ll) return CMG_ERR_TOO_LARGE;
+    const size_t isz = L.col16 ? 2 : 4, esz = fp32 ? 4 : 8;
+    CMG_TRY(dev_alloc_n(&L.meta, (size_t)std::max<long long>(tm, 1), s));
+    CMG_TRY(dev_alloc(&L.bcol, isz * (size_t)std::max<long long>(te, 1), s));
+    CMG_TRY(dev_alloc(&L.bw, esz * (size_t)std::max<long long>(te, 1), s));
+    k_layout_meta<<<wblocks, 256, 0, s>>>(G, L.voff, L.rp, L.perm, L.heavy, L.moff, L.meta);
+    CMG_TRY(launch_status());
+    const int fb = grid_for(N, 256);
+#define CMG_FILL(T, I)                                                                            \
+    k_layout_fill<T, I><<<fb, 256, 0, s>>>(N, G, L.voff, L.rp, L.col, L.w, L.perm, L.inv, L.heavy, \
+                                           L.eoff, L.moff, L.meta, reinterpret_cast<I *>(L.bcol),   \
+                                           reinterpret_cast<T *>(L.bw))
+    if (fp32 && L.col16) CMG_FILL(float, uint16_t);
+    else if (fp32) CMG_FILL(float, int);
+    else if (L.col16) CMG_FILL(double, uint16_t);
+    else CMG_FILL(double, int);
+#undef CMG_FILL
+    CMG_TRY(launch_status());
+    *bytes += (size_t)N * 8 + (size_t)G * 12 + (size_t)tm * 4 + (size_t)te * (isz + esz);
+    return CMG_OK;
+}
+
 // Level lists: graphs with J >= j, ordered by decreasing n + nnz on level j.
 static cmg_status_t build_lists(cmg_batch_s *b, cudaStream_t s) {
     const int G = b->G;
@@ -833,9 +1107,9 @@ static cmg_status_t build_lists(cmg_batch_s *b, cudaStream_t s) {
             if (b->J[q] < j) continue;
             ids.push_back(q);
             const long long n = L.hvoff[q + 1] - L.hvoff[q];
-            const long long m = L.heoff[q + 1] - L.heoff[q];
+            const long long isz = L.col16 ? 2 : 4;
             L.max_vbytes = std::max(L.max_vbytes, n * (2 * esz + (fp32 ? 0 : 8)));
-            L.max_cbytes = std::max(L.max_cbytes, 4 * (n + 1) + m * (4 + esz));
+            L.max_cbytes = std::max(L.max_cbytes, (long long)L.hecnt[q] * (esz + isz) + 4ll * L.hmcnt[q] + 16);
         }
         std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
             const long long wx = (L.hvoff[x + 1] - L.hvoff[x]) + (long long)(L.heoff[x + 1] - L.heoff[x]);
@@ -1013,11 +1287,7 @@ static cmg_status_t build_batch(cmg_batch_s *b, const int64_t *offs, const int64
         bytes += sizeof(int) * ((size_t)V.n + 1) + (sizeof(int) + sizeof(double)) * (size_t)V.nnz;
         bytes += sizeof(int) * (G + 1) + sizeof(double) * G;
         if (V.agg) bytes += sizeof(int) * (size_t)V.n;
-        if (fp32) {
-            CMG_TRY(dev_alloc_n(&V.w32, (size_t)std::max<long long>(V.nnz, 1), s));
-            CMG_TRY(launch_to_float(V.nnz, V.w, V.w32, s));
-            bytes += sizeof(float) * (size_t)V.nnz;
-        }
+        CMG_TRY(build_layout(b, j, s, &bytes));
         if (j > 0) {
             CMG_TRY(dev_alloc(&V.u, esz * (size_t)std::max(V.n, 1), s));
             bytes += esz * (size_t)V.n;
@@ -1291,7 +1561,7 @@ extern "C" cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t s
         const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
         int per_sm = 0;
         const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)batch_kernel(fp32, shape->lanes_per_row), threads_for_gpc(*shape),
+            &per_sm, (const void *)batch_kernel(fp32, b->lv[level].col16, shape->lanes_per_row), threads_for_gpc(*shape),
             (size_t)b->lv[level].smem_group * shape->graphs_per_cta);
         if (e != cudaSuccess || per_sm < 1) st = CMG_ERR_INVALID_ARG;
     }
@@ -1321,7 +1591,7 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
         int per_sm = 0;
         const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
         CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)batch_kernel(fp32, sh.lanes_per_row), threads_for_gpc(sh),
+            &per_sm, (const void *)batch_kernel(fp32, V.col16, sh.lanes_per_row), threads_for_gpc(sh),
             (size_t)V.smem_group * sh.graphs_per_cta));
         if (per_sm < 1) {
             *ms = 1e30f;

@@ -17,6 +17,9 @@ namespace cmg {
 
 // ----------------------------------------------------------------- errors
 cmg_status_t from_cuda(cudaError_t e);
+// from_cuda for the call at file:line; with CMG_DEBUG_ERRORS set in the
+// environment the failing call is reported on stderr.
+cmg_status_t from_cuda_at(cudaError_t e, const char *file, int line);
 
 #define CMG_TRY(expr)                                                        \
     do {                                                                     \
@@ -27,7 +30,7 @@ cmg_status_t from_cuda(cudaError_t e);
 #define CMG_CUDA(expr)                                                       \
     do {                                                                     \
         cudaError_t _ce = (expr);                                            \
-        if (_ce != cudaSuccess) return ::cmg::from_cuda(_ce);                \
+        if (_ce != cudaSuccess) return ::cmg::from_cuda_at(_ce, __FILE__, __LINE__); \
     } while (0)
 
 // Status of the last kernel launch (launch-configuration errors only); also
@@ -220,6 +223,12 @@ inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Grid size for a plain grid-stride kernel: enough CTAs to cover `work`
 // items at `per_cta` items each, at most `waves` full waves of the GPU.
 int grid_for(long long work, int per_cta, int waves = 8);
+
+// Lets `kernel` take up to the device's opt-in maximum of dynamic shared
+// memory.  Every caller sets the same value, so threads launching the kernel
+// concurrently with different shared-memory sizes never lower the limit
+// under one another.
+cmg_status_t allow_max_dynamic_smem(const void *kernel);
 
 // Largest co-resident grid for a cooperative launch of `kernel`.
 cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out);

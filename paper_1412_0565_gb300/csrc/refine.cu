@@ -927,7 +927,7 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
         const int G = small_lanes(lv.n, lv.nnz, run.fp32);
         const void *kern = run.fp32 ? small_kernel<float>(G) : small_kernel<double>(G);
         const size_t smem = small_bytes(lv, G, run.fp32);
-        CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        CMG_TRY(allow_max_dynamic_smem(kern));
         return coop_launch(kern, 1, small_threads(lv.n, G), smem, s, args, gs);
     }
     if (!run.fp32 && !run.gd) return CMG_ERR_INVALID_ARG;
@@ -945,7 +945,7 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     }
     const void *kern = run.fp32 ? (const void *)k_power_tiled<float> : (const void *)k_power_tiled<double>;
     const size_t smem = tiled_smem(run.fp32 != 0);
-    CMG_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    CMG_TRY(allow_max_dynamic_smem(kern));
     int maxb = 0;
     CMG_TRY(coop_max_blocks(kern, kTileThreads, smem, &maxb));
     // one tile per CTA where possible (each tile's phases are latency-bound),

@@ -1,5 +1,8 @@
 // runtime.cu -- error mapping, the library's device memory pool, device
 // properties and cooperative-launch helpers.
+#include <stdio.h>
+#include <stdlib.h>
+
 #include <atomic>
 #include <mutex>
 
@@ -14,13 +17,21 @@ cmg_status_t from_cuda(cudaError_t e) {
     return CMG_ERR_CUDA;
 }
 
+cmg_status_t from_cuda_at(cudaError_t e, const char *file, int line) {
+    if (e != cudaSuccess) {
+        static const bool report = getenv("CMG_DEBUG_ERRORS") != nullptr;
+        if (report) fprintf(stderr, "cmg: %s at %s:%d\n", cudaGetErrorName(e), file, line);
+    }
+    return from_cuda(e);
+}
+
 namespace {
 std::atomic<unsigned long long> g_launches{0};
 }
 
 cmg_status_t launch_status() {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    return from_cuda(cudaGetLastError());
+    return from_cuda_at(cudaGetLastError(), "kernel launch", 0);
 }
 
 unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
@@ -118,6 +129,17 @@ int grid_for(long long work, int per_cta, int waves) {
     if (b > cap) b = cap;
     if (b < 1) b = 1;
     return (int)b;
+}
+
+cmg_status_t allow_max_dynamic_smem(const void *kernel) {
+    DeviceInfo d;
+    CMG_TRY(device_info(&d));
+    // static plus dynamic shared memory may not exceed the opt-in maximum
+    cudaFuncAttributes fa;
+    CMG_CUDA(cudaFuncGetAttributes(&fa, kernel));
+    const int dyn = d.max_smem_optin - (int)fa.sharedSizeBytes;
+    CMG_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    return CMG_OK;
 }
 
 cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out) {

@@ -15,6 +15,8 @@
 // A request's result does not depend on the job it ran in beyond rounding:
 // the batched form computes each graph's hierarchy bit for bit as the single
 // form does.
+#include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -175,8 +177,15 @@ Job pick_job(cmg_server_s *S) {
         job.reserve = total;
         S->used += total;
         for (auto jt : take) job.reqs.push_back(*jt);
-        // erase from the back so the earlier iterators stay valid
-        for (auto k = take.rbegin(); k != take.rend(); ++k) S->pending.erase(*k);
+        // an erase inside a deque invalidates every iterator: rebuild the
+        // queue without the taken requests instead
+        std::deque<Request *> rest;
+        size_t t = 0;
+        for (Request *x : S->pending) {
+            if (t < job.reqs.size() && x == job.reqs[t]) t++;
+            else rest.push_back(x);
+        }
+        S->pending.swap(rest);
         return job;
     }
     return job;
@@ -265,7 +274,16 @@ void run_job(cmg_server_s *S, Job &job, cudaStream_t s) {
     S->stats.batch_jobs++;
 }
 
-void worker_main(cmg_server_s *S, cudaStream_t s) {
+// With CMG_DEBUG_SERVE set in the environment, job events go to stderr.
+void trace(const char *what, const Job &job, int worker, int status) {
+    static const bool on = getenv("CMG_DEBUG_SERVE") != nullptr;
+    if (!on) return;
+    fprintf(stderr, "cmg-serve %llu w%d %s kind=%d n=%zu first_gid=%lld status=%d\n",
+            (unsigned long long)(now_ns() / 1000), worker, what, job.kind, job.reqs.size(),
+            job.reqs.empty() ? -1ll : (long long)job.reqs[0]->gid, status);
+}
+
+void worker_main(cmg_server_s *S, cudaStream_t s, int worker) {
     cudaSetDevice(S->device);
     for (;;) {
         Job job;
@@ -281,7 +299,9 @@ void worker_main(cmg_server_s *S, cudaStream_t s) {
             S->running++;
             S->peak = std::max(S->peak, S->used);
         }
+        trace("start", job, worker, 0);
         run_job(S, job, s);
+        trace("end", job, worker, job.reqs[0]->res.status);
         {
             std::lock_guard<std::mutex> lk(S->mu);
             S->running--;
@@ -347,7 +367,7 @@ extern "C" cmg_status_t cmg_server_create(const cmg_server_config_t *cfg, const 
         }
         S->streams.push_back(st);
     }
-    for (int k = 0; k < c.workers; k++) S->workers.emplace_back(worker_main, S, S->streams[k]);
+    for (int k = 0; k < c.workers; k++) S->workers.emplace_back(worker_main, S, S->streams[k], k);
     *out = S;
     return CMG_OK;
 }
@@ -393,18 +413,32 @@ extern "C" cmg_status_t cmg_server_submit(cmg_server_t S, int64_t graph_id, doub
     return CMG_OK;
 }
 
-extern "C" cmg_status_t cmg_server_wait(cmg_server_t S, int64_t ticket, cmg_request_t *out) {
+static cmg_status_t wait_impl(cmg_server_t S, int64_t ticket, int64_t timeout_ms, cmg_request_t *out) {
     if (!S) return CMG_ERR_INVALID_ARG;
     std::unique_lock<std::mutex> lk(S->mu);
     auto it = S->reqs.find(ticket);
     if (it == S->reqs.end()) return CMG_ERR_INVALID_ARG;
     Request *r = it->second;
-    S->cv_done.wait(lk, [&] { return r->done; });
+    if (timeout_ms < 0) {
+        S->cv_done.wait(lk, [&] { return r->done; });
+    } else if (!S->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), [&] { return r->done; })) {
+        return CMG_ERR_TIMEOUT;
+    }
     if (out) *out = r->res;
     S->reqs.erase(it);
     const cmg_status_t st = (cmg_status_t)r->res.status;
     delete r;
     return st;
+}
+
+extern "C" cmg_status_t cmg_server_wait(cmg_server_t S, int64_t ticket, cmg_request_t *out) {
+    return wait_impl(S, ticket, -1, out);
+}
+
+extern "C" cmg_status_t cmg_server_wait_for(cmg_server_t S, int64_t ticket, int64_t timeout_ms,
+                                            cmg_request_t *out) {
+    if (timeout_ms < 0) return CMG_ERR_INVALID_ARG;
+    return wait_impl(S, ticket, timeout_ms, out);
 }
 
 extern "C" cmg_status_t cmg_server_get_stats(cmg_server_t S, cmg_server_stats_t *out) {

@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "csr_from_edges", "grid2d", "grid3d", "path", "cycle", "complete", "star",
     "random_connected", "chung_lu", "rgg", "barabasi_albert", "largest_component",
-    "batch_graphs", "concat_csr", "serving_sizes",
+    "batch_graphs", "concat_csr", "serving_sizes", "serving_graphs",
 ]
 
 
@@ -318,3 +318,24 @@ def serving_sizes(count: int, lo: float = 1e3, hi: float = 2e6, seed: int = 1412
         x = rng.normal(mu, sd, size=count)
         out.extend(x[(x >= a) & (x <= b)].tolist())
     return np.exp(np.array(out[:count])).astype(np.int64)
+
+
+def serving_graphs(count: int, lo: float = 1e3, hi: float = 2e6, seed: int = 1412,
+                   workers: int = 0):
+    """Graphs of a serving workload: sizes from serving_sizes, families and
+    weights as in batch_graphs (graph i is family i mod 3)."""
+    sizes = serving_sizes(count, lo, hi, seed)
+    items = [(i, int(nv)) for i, nv in enumerate(sizes)]
+    if workers <= 1:
+        return _family_chunk((seed + 7, items))
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    # largest first, so the pool's chunks are balanced
+    order = sorted(items, key=lambda t: -t[1])
+    chunks = [order[k::workers] for k in range(workers)]
+    out = [None] * count
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for chunk, res in zip(chunks, ex.map(_family_chunk, [(seed + 7, c) for c in chunks])):
+            for (i, _), g in zip(chunk, res):
+                out[i] = g
+    return out

@@ -49,10 +49,10 @@ def run_all(server, gids, concurrent):
     if concurrent:
         tickets = [(g, server.submit(g)) for g in gids]
         for g, t in tickets:
-            out[g] = server.wait(t)
+            out[g] = server.wait(t, timeout_s=300)
     else:
         for g in gids:
-            out[g] = server.wait(server.submit(g))
+            out[g] = server.wait(server.submit(g), timeout_s=300)
     return out
 
 
@@ -126,3 +126,36 @@ def test_request_that_can_never_fit_fails_cleanly():
         with pytest.raises(cmg.CmgError) as e:
             srv.wait(srv.submit(gid))
         assert e.value.name == "ERR_TOO_LARGE"
+
+
+def test_repeated_graphs_under_poisson_arrivals_all_complete():
+    """A request trace that repeats graphs, arriving over time: every request
+    completes once (no request lost or run twice), results equal the alone
+    results; waits are bounded so a lost request fails instead of hanging."""
+    import time
+    gs = graphs()
+    rng = np.random.default_rng(5)
+    trace = rng.integers(0, len(gs), size=40)
+    alone = {}
+    with cmg.Server(workers=1, max_batch=1, seed=1412) as srv:
+        ids = [srv.add_graph(*g) for g in gs]
+        for k in sorted(set(trace.tolist())):
+            alone[k] = srv.wait(srv.submit(ids[k]), timeout_s=120)
+    with cmg.Server(workers=4, max_batch=64, batch_max_n=5000, seed=1412) as srv:
+        ids = [srv.add_graph(*g) for g in gs]
+        arr = np.cumsum(rng.exponential(0.004, size=len(trace)))
+        t0 = time.perf_counter()
+        tickets = []
+        for k, ta in zip(trace, arr):
+            d = t0 + ta - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append((k, srv.submit(ids[k])))
+        for k, t in tickets:
+            u, r = srv.wait(t, timeout_s=120)
+            assert r["status"] == "OK"
+            assert aligned_err(u, alone[k][0]) <= VEC_TOL, k
+            assert abs(r["lambda2"] - alone[k][1]["lambda2"]) <= LAM_TOL * abs(alone[k][1]["lambda2"])
+        st = srv.stats()
+        assert st["completed"] == len(trace)
+        assert st["single_jobs"] + st["warm_jobs"] + st["batch_jobs"] <= len(trace)
