@@ -90,6 +90,8 @@ struct LevelData {
     int ntiles = 0;
     long long sell_nnz = 0;
     double g = 0.0;
+    bool has_lay = false;   // large level: sweeps read the sweep layout
+    SweepLayout lay;
 };
 
 struct cmg_hierarchy_s {
@@ -114,6 +116,7 @@ static void free_level(LevelData &L, cudaStream_t s) {
     dev_free(L.w32, s);
     dev_free(L.agg, s);
     dev_free(L.tiles, s);
+    free_sweep_layout(L.lay, s);
     L = LevelData();
 }
 
@@ -214,6 +217,23 @@ cmg_status_t cmg::launch_to_float(long long m, const double *w, float *w32, cuda
     return launch_status();
 }
 
+static PiLevel level_view(const LevelData &L) {
+    PiLevel v;
+    v.n = L.n;
+    v.nnz = L.nnz;
+    v.rp = L.rp;
+    v.col = L.col;
+    v.w = L.w;
+    v.w32 = L.w32;
+    v.g = L.g;
+    v.agg = L.agg;
+    v.tile_row = L.tiles;
+    v.ntiles = L.ntiles;
+    v.sell_nnz = L.sell_nnz;
+    v.lay = L.has_lay ? &L.lay : nullptr;
+    return v;
+}
+
 static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t *row_ptr,
                                     const int32_t *col, const double *w, int32_t mem) {
     cudaStream_t s = h->stream;
@@ -306,15 +326,23 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
             CMG_TRY(launch_to_float(L.nnz, L.w, L.w32, s));
         }
     }
-    // ---- row tiles (large levels) and SELL-32 sizes (small levels)
+    // ---- SELL-32 sizes (small levels); sweep layouts for the levels the
+    // shared-memory kernel cannot hold
+    size_t lay_bytes = 0;
     {
         unsigned long long *cnt;
+        int *voff1;
         CMG_TRY(scr.get(&cnt, 1));
+        CMG_TRY(scr.get(&voff1, 2));
+        const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
         for (auto &L : h->lv) {
-            L.ntiles = tile_count(L.n, L.nnz);
-            CMG_TRY(dev_alloc_n(&L.tiles, (size_t)L.ntiles + 1, s));
-            CMG_TRY(build_tiles(L.n, L.nnz, L.rp, L.tiles, s));
             if (&L == &h->lv.front() && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
+            if (small_level_fits(level_view(L), fp32)) continue;
+            const int hv[2] = {0, L.n};
+            CMG_CUDA(cudaMemcpyAsync(voff1, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
+            CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, fp32,
+                                       &L.lay, &lay_bytes, s));
+            L.has_lay = true;
         }
     }
     // ---- solve workspace: a buffer pair per level, results, barrier state
@@ -343,7 +371,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         if (o.precision == CMG_PRECISION_FP64) bytes += sizeof(double) * (size_t)L.n;
     }
     bytes += sizeof(double) * (size_t)n;
-    h->bytes = bytes;
+    h->bytes = bytes + lay_bytes;
     CMG_CUDA(cudaStreamSynchronize(s));
     return CMG_OK;
 }
@@ -415,21 +443,6 @@ cmg_status_t cmg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, co
     return CMG_OK;
 }
 
-static PiLevel level_view(const LevelData &L) {
-    PiLevel v;
-    v.n = L.n;
-    v.nnz = L.nnz;
-    v.rp = L.rp;
-    v.col = L.col;
-    v.w = L.w;
-    v.w32 = L.w32;
-    v.g = L.g;
-    v.agg = L.agg;
-    v.tile_row = L.tiles;
-    v.ntiles = L.ntiles;
-    v.sell_nnz = L.sell_nnz;
-    return v;
-}
 
 cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double *lambda2_out,
                          cmg_stats_t *stats_out, void *stream) {
@@ -471,6 +484,7 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
             for (int k = 0; k < 3; k++) r.coarse_bufs[k] = h->bufs[3 * (j + 1) + k];
             r.coarse_res = h->res + (j + 1);
             r.coarse_agg = h->lv[j].agg;
+            r.coarse_inv = h->lv[j + 1].has_lay ? h->lv[j + 1].lay.inv : nullptr;
         }
         for (int k = 0; k < 3; k++) r.bufs[k] = h->bufs[3 * j + k];
         r.gd = h->gd[j];

@@ -102,16 +102,6 @@ constexpr int kOffInt = kOffDred + 32 * 4 * (int)sizeof(double);
 constexpr int kBatchMaxThreads = 512;
 static_assert(kOffInt + 64 <= kGroupHeader, "group header too small");
 
-// Sweep layout of a level, per graph (built at setup): rows renumbered by
-// decreasing degree (stable); the rows with more than kHeavy entries come
-// first and keep CSR form ("heavy" rows), the others form slices of 32 rows
-// whose entries are interleaved -- entry k of the slice's row l sits at
-// slice_offset + 32 k + l, shorter rows padded with weight 0 -- so a warp
-// reads a slice with coalesced loads that do not depend on each other.
-// Columns are renumbered local ids (16-bit when every graph of the level
-// has at most 65536 vertices).  meta of a graph: h + 1 heavy row pointers,
-// then nsl + 1 slice offsets (entry offsets local to the graph).
-constexpr int kHeavy = 32;
 
 struct BatchPiArgs {
     int level;
@@ -253,7 +243,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
         const int h = a.heavy[q];
         const int nsl = (n - h + 31) >> 5;
         const int *gmeta = a.meta + a.moff[q];
-        const int nm = h + nsl + 2;
+        const int nm = h + nsl + 1;
         const int ne = gmeta[nm - 1];
         const double gsh = a.gsh[q];
         const bool coarsest = a.level == a.J[q];
@@ -314,7 +304,7 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
             C = reinterpret_cast<const IDX *>(a.bcol) + a.eoff[q];
             W = reinterpret_cast<const T *>(a.bw) + a.eoff[q];
         }
-        const int *SO = M + h + 1;   // slice offsets
+        const int *SO = M + h;       // slice offsets
         gbar(bid, tg);
 
         // ---- start vector (renumbered rows): Gaussian (Alg. 1 Step 2) or
@@ -622,156 +612,6 @@ static BatchKernel batch_kernel(int fp32, int col16, int G) {
     return col16 ? batch_kernel_ti<double, uint16_t>(G) : batch_kernel_ti<double, int>(G);
 }
 
-// ------------------------------------------------------------------ layout kernels
-// keys (graph, decreasing degree) of every union vertex, for a stable sort
-__global__ void k_layout_keys(int n, int G, const int *__restrict__ voff, const int *__restrict__ rp,
-                              uint64_t *__restrict__ keys, uint32_t *__restrict__ vals) {
-    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (voff[mid] <= v) lo = mid;
-            else hi = mid - 1;
-        }
-        const uint32_t deg = (uint32_t)(rp[v + 1] - rp[v]);
-        keys[v] = ((uint64_t)lo << 32) | (uint64_t)(0xffffffffu - deg);
-        vals[v] = (uint32_t)v;
-    }
-}
-
-__global__ void k_layout_inv(int n, const uint32_t *__restrict__ perm, int *__restrict__ inv) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x)
-        inv[perm[p]] = p;
-}
-
-__device__ __forceinline__ int perm_deg(const int *rp, const uint32_t *perm, int p) {
-    const int v = (int)perm[p];
-    return rp[v + 1] - rp[v];
-}
-
-// Per graph (one warp): heavy rows h, layout entries and meta words.
-__global__ void k_layout_count(int G, const int *__restrict__ voff, const int *__restrict__ rp,
-                               const uint32_t *__restrict__ perm, int *__restrict__ heavy,
-                               int *__restrict__ ecnt, int *__restrict__ mcnt) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < G; q += warps) {
-        const int v0 = voff[q], n = voff[q + 1] - v0;
-        int h = 0, he = 0;
-        for (int p = lane; p < n; p += 32) {
-            const int d = perm_deg(rp, perm, v0 + p);
-            if (d > kHeavy) {
-                h++;
-                he += d;
-            }
-        }
-        h = warp_sum_int(h);
-        he = warp_sum_int(he);
-        const int nsl = (n - h + 31) >> 5;
-        int se = 0;
-        for (int sl = lane; sl < nsl; sl += 32) se += 32 * perm_deg(rp, perm, v0 + h + 32 * sl);
-        se = warp_sum_int(se);
-        if (lane == 0) {
-            heavy[q] = h;
-            ecnt[q] = he + se;
-            mcnt[q] = h + nsl + 2;
-        }
-    }
-}
-
-// Per graph (one warp): heavy row pointers, then slice offsets.
-__global__ void k_layout_meta(int G, const int *__restrict__ voff, const int *__restrict__ rp,
-                              const uint32_t *__restrict__ perm, const int *__restrict__ heavy,
-                              const int *__restrict__ moff, int *__restrict__ meta) {
-    const int lane = threadIdx.x & 31;
-    const int warps = (gridDim.x * blockDim.x) >> 5;
-    for (int q = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; q < G; q += warps) {
-        const int v0 = voff[q], n = voff[q + 1] - v0, h = heavy[q];
-        const int nsl = (n - h + 31) >> 5;
-        int *m = meta + moff[q];
-        const int items = h + nsl;   // heavy rows, then slices
-        int run = 0;
-        for (int t0 = 0; t0 < items; t0 += 32) {
-            const int t = t0 + lane;
-            int len = 0;
-            if (t < h) len = perm_deg(rp, perm, v0 + t);
-            else if (t < items) len = 32 * perm_deg(rp, perm, v0 + h + 32 * (t - h));
-            int x = len;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            const int excl = run + x - len;
-            // heavy row t starts at excl (meta word t); slice t-h starts at excl
-            // (meta word h + 1 + t - h)
-            if (t < h) m[t] = excl;
-            else if (t < items) m[t + 1] = excl;
-            run += __shfl_sync(0xffffffffu, x, 31);
-        }
-        if (lane == 0) {
-            // end of the heavy rows = start of the first slice
-            int he = 0;
-            for (int t = 0; t < h; t++) he += perm_deg(rp, perm, v0 + t);
-            m[h] = he;
-            m[h + 1 + nsl] = run;
-        }
-    }
-}
-
-// Entries of every renumbered row; the last slice's phantom rows (past n) and
-// short rows are padded with weight 0 and a valid column.
-template <typename T, typename IDX>
-__global__ void k_layout_fill(int n, int G, const int *__restrict__ voff, const int *__restrict__ rp,
-                              const int *__restrict__ col, const double *__restrict__ w,
-                              const uint32_t *__restrict__ perm, const int *__restrict__ inv,
-                              const int *__restrict__ heavy, const int *__restrict__ eoff,
-                              const int *__restrict__ moff, const int *__restrict__ meta,
-                              IDX *__restrict__ bcol, T *__restrict__ bw) {
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n; p += gridDim.x * blockDim.x) {
-        int lo = 0, hi = G - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (voff[mid] <= p) lo = mid;
-            else hi = mid - 1;
-        }
-        const int q = lo, v0 = voff[q], ng = voff[q + 1] - v0, r = p - v0, h = heavy[q];
-        const int *m = meta + moff[q];
-        const int v = (int)perm[p];
-        const int e0 = rp[v], deg = rp[v + 1] - e0;
-        IDX *gc = bcol + eoff[q];
-        T *gw = bw + eoff[q];
-        if (r < h) {
-            const int d0 = m[r];
-            for (int j = 0; j < deg; j++) {
-                gc[d0 + j] = (IDX)(inv[col[e0 + j]] - v0);
-                gw[d0 + j] = (T)w[e0 + j];
-            }
-            continue;
-        }
-        const int sl = (r - h) >> 5, l = (r - h) & 31;
-        const int so = m[h + 1 + sl], wd = (m[h + 2 + sl] - so) >> 5;
-        for (int j = 0; j < wd; j++) {
-            const int d = so + 32 * j + l;
-            if (j < deg) {
-                gc[d] = (IDX)(inv[col[e0 + j]] - v0);
-                gw[d] = (T)w[e0 + j];
-            } else {
-                gc[d] = (IDX)r;
-                gw[d] = (T)0;
-            }
-        }
-        // the graph's last row also pads the phantom rows of its last slice
-        if (r == ng - 1) {
-            for (int l2 = l + 1; l2 < 32; l2++)
-                for (int j = 0; j < wd; j++) {
-                    gc[so + 32 * j + l2] = (IDX)0;
-                    gw[so + 32 * j + l2] = (T)0;
-                }
-        }
-    }
-}
-
 }  // namespace cmg
 
 // ================================================================== host side
@@ -786,14 +626,7 @@ struct BLevel {
     int *col = nullptr;
     double *w = nullptr;
     int *agg = nullptr;          // onto the next union level
-    // sweep layout (rows renumbered by degree; heavy CSR rows + 32-row slices)
-    uint32_t *perm = nullptr;    // new union position -> original union vertex
-    int *inv = nullptr;
-    int *heavy = nullptr, *eoff = nullptr, *moff = nullptr, *meta = nullptr;
-    void *bcol = nullptr;        // uint16 (col16) or int32 local columns
-    void *bw = nullptr;          // sweep-precision weights
-    int col16 = 1;
-    std::vector<int> hecnt, hmcnt;   // per-graph layout entries and meta words
+    SweepLayout lay;             // sweep layout of the level
     int *voff = nullptr;         // device int[G+1]
     double *gsh = nullptr;       // device double[G]
     std::vector<int> hvoff;      // host copies
@@ -814,14 +647,7 @@ void free_blevel(BLevel &L, cudaStream_t s) {
     dev_free(L.rp, s);
     dev_free(L.col, s);
     dev_free(L.w, s);
-    dev_free(L.perm, s);
-    dev_free(L.inv, s);
-    dev_free(L.heavy, s);
-    dev_free(L.eoff, s);
-    dev_free(L.moff, s);
-    dev_free(L.meta, s);
-    dev_free(L.bcol, s);
-    dev_free(L.bw, s);
+    free_sweep_layout(L.lay, s);
     dev_free(L.agg, s);
     dev_free(L.voff, s);
     dev_free(L.gsh, s);
@@ -946,7 +772,7 @@ static cmg_status_t level_workspace(cmg_batch_s *b, int j, cudaStream_t s) {
             b->bytes += sizeof(double) * (size_t)L.n;
         }
     }
-    BatchKernel kern = batch_kernel(fp32, L.col16, L.shape.lanes_per_row);
+    BatchKernel kern = batch_kernel(fp32, L.lay.col16, L.shape.lanes_per_row);
     if (!kern) return CMG_ERR_INVALID_ARG;
     const int smem = L.smem_group * L.shape.graphs_per_cta;
     if (smem > di.max_smem_optin) return CMG_ERR_INVALID_ARG;
@@ -959,7 +785,7 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     if (L.count == 0) return CMG_OK;
     const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
     const cmg_options_t &o = b->opts;
-    BatchKernel kern = batch_kernel(fp32, L.col16, L.shape.lanes_per_row);
+    BatchKernel kern = batch_kernel(fp32, L.lay.col16, L.shape.lanes_per_row);
     const int threads = threads_for_gpc(L.shape);
     const int smem = L.smem_group * L.shape.graphs_per_cta;
     int per_sm = 0;
@@ -974,14 +800,14 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     a.rp = L.rp;
     a.col = L.col;
     a.w = L.w;
-    a.perm = reinterpret_cast<const int *>(L.perm);
-    a.inv = L.inv;
-    a.heavy = L.heavy;
-    a.eoff = L.eoff;
-    a.moff = L.moff;
-    a.meta = L.meta;
-    a.bcol = L.bcol;
-    a.bw = L.bw;
+    a.perm = reinterpret_cast<const int *>(L.lay.perm);
+    a.inv = L.lay.inv;
+    a.heavy = L.lay.heavy;
+    a.eoff = L.lay.eoff;
+    a.moff = L.lay.moff;
+    a.meta = L.lay.meta;
+    a.bcol = L.lay.bcol;
+    a.bw = L.lay.bw;
     a.voff = L.voff;
     a.gsh = L.gsh;
     a.list = L.list;
@@ -1022,76 +848,11 @@ static cmg_status_t enqueue_solve(cmg_batch_s *b, int force_k, cudaStream_t s) {
     return CMG_OK;
 }
 
-// Sweep layout of union level j (see k_layout_*): stable sort of the rows by
-// (graph, decreasing degree), per-graph counts, offsets, then the entries.
+// Sweep layout of union level j (see SweepLayout).
 static cmg_status_t build_layout(cmg_batch_s *b, int j, cudaStream_t s, size_t *bytes) {
     BLevel &L = b->lv[j];
-    const int G = b->G, N = L.n;
-    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
-    int maxn = 0;
-    for (int q = 0; q < G; q++) maxn = std::max(maxn, L.hvoff[q + 1] - L.hvoff[q]);
-    L.col16 = maxn <= 65536 ? 1 : 0;
-    Scratch scr(s);
-    uint64_t *ka, *kb;
-    uint32_t *va, *vb;
-    int *cnt_n, *ecnt, *mcnt;
-    CMG_TRY(scr.get(&ka, (size_t)N));
-    CMG_TRY(scr.get(&kb, (size_t)N));
-    CMG_TRY(scr.get(&va, (size_t)N));
-    CMG_TRY(scr.get(&vb, (size_t)N));
-    CMG_TRY(scr.get(&cnt_n, 1));
-    CMG_TRY(scr.get(&ecnt, (size_t)G));
-    CMG_TRY(scr.get(&mcnt, (size_t)G));
-    CMG_CUDA(cudaMemcpyAsync(cnt_n, &L.n, sizeof(int), cudaMemcpyHostToDevice, s));
-    k_layout_keys<<<grid_for(N, 256), 256, 0, s>>>(N, G, L.voff, L.rp, ka, va);
-    CMG_TRY(launch_status());
-    CMG_TRY(radix_sort_pairs(&ka, &va, kb, vb, N, cnt_n, 32 + bits_for(G), scr, s));
-    CMG_TRY(dev_alloc_n(&L.perm, (size_t)N, s));
-    CMG_TRY(dev_alloc_n(&L.inv, (size_t)N, s));
-    CMG_CUDA(cudaMemcpyAsync(L.perm, va, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
-    k_layout_inv<<<grid_for(N, 256), 256, 0, s>>>(N, L.perm, L.inv);
-    CMG_TRY(launch_status());
-    CMG_TRY(dev_alloc_n(&L.heavy, (size_t)G, s));
-    CMG_TRY(dev_alloc_n(&L.eoff, (size_t)G + 1, s));
-    CMG_TRY(dev_alloc_n(&L.moff, (size_t)G + 1, s));
-    const int wblocks = grid_for((long long)G * 32, 256);
-    k_layout_count<<<wblocks, 256, 0, s>>>(G, L.voff, L.rp, L.perm, L.heavy, ecnt, mcnt);
-    CMG_TRY(launch_status());
-    CMG_TRY(exclusive_scan(ecnt, L.eoff, G, scr, s));
-    CMG_TRY(exclusive_scan(mcnt, L.moff, G, scr, s));
-    L.hecnt.resize(G);
-    L.hmcnt.resize(G);
-    int tot[2] = {0, 0};
-    CMG_CUDA(cudaMemcpyAsync(L.hecnt.data(), ecnt, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaMemcpyAsync(L.hmcnt.data(), mcnt, sizeof(int) * G, cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaMemcpyAsync(&tot[0], L.eoff + G, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaMemcpyAsync(&tot[1], L.moff + G, sizeof(int), cudaMemcpyDeviceToHost, s));
-    CMG_CUDA(cudaStreamSynchronize(s));
-    long long te = 0, tm = 0;
-    for (int q = 0; q < G; q++) {
-        te += L.hecnt[q];
-        tm += L.hmcnt[q];
-    }
-    if (te != tot[0] || tm != tot[1] || te >= 2147483647ll) return CMG_ERR_TOO_LARGE;
-    const size_t isz = L.col16 ? 2 : 4, esz = fp32 ? 4 : 8;
-    CMG_TRY(dev_alloc_n(&L.meta, (size_t)std::max<long long>(tm, 1), s));
-    CMG_TRY(dev_alloc(&L.bcol, isz * (size_t)std::max<long long>(te, 1), s));
-    CMG_TRY(dev_alloc(&L.bw, esz * (size_t)std::max<long long>(te, 1), s));
-    k_layout_meta<<<wblocks, 256, 0, s>>>(G, L.voff, L.rp, L.perm, L.heavy, L.moff, L.meta);
-    CMG_TRY(launch_status());
-    const int fb = grid_for(N, 256);
-#define CMG_FILL(T, I)                                                                            \
-    k_layout_fill<T, I><<<fb, 256, 0, s>>>(N, G, L.voff, L.rp, L.col, L.w, L.perm, L.inv, L.heavy, \
-                                           L.eoff, L.moff, L.meta, reinterpret_cast<I *>(L.bcol),   \
-                                           reinterpret_cast<T *>(L.bw))
-    if (fp32 && L.col16) CMG_FILL(float, uint16_t);
-    else if (fp32) CMG_FILL(float, int);
-    else if (L.col16) CMG_FILL(double, uint16_t);
-    else CMG_FILL(double, int);
-#undef CMG_FILL
-    CMG_TRY(launch_status());
-    *bytes += (size_t)N * 8 + (size_t)G * 12 + (size_t)tm * 4 + (size_t)te * (isz + esz);
-    return CMG_OK;
+    return build_sweep_layout(b->G, L.voff, L.hvoff, L.n, L.rp, L.col, L.w,
+                              b->opts.precision == CMG_PRECISION_FP32_SWEEP, &L.lay, bytes, s);
 }
 
 // Level lists: graphs with J >= j, ordered by decreasing n + nnz on level j.
@@ -1107,9 +868,9 @@ static cmg_status_t build_lists(cmg_batch_s *b, cudaStream_t s) {
             if (b->J[q] < j) continue;
             ids.push_back(q);
             const long long n = L.hvoff[q + 1] - L.hvoff[q];
-            const long long isz = L.col16 ? 2 : 4;
+            const long long isz = L.lay.col16 ? 2 : 4;
             L.max_vbytes = std::max(L.max_vbytes, n * (2 * esz + (fp32 ? 0 : 8)));
-            L.max_cbytes = std::max(L.max_cbytes, (long long)L.hecnt[q] * (esz + isz) + 4ll * L.hmcnt[q] + 16);
+            L.max_cbytes = std::max(L.max_cbytes, (long long)L.lay.hecnt[q] * (esz + isz) + 4ll * L.lay.hmcnt[q] + 16);
         }
         std::stable_sort(ids.begin(), ids.end(), [&](int x, int y) {
             const long long wx = (L.hvoff[x + 1] - L.hvoff[x]) + (long long)(L.heoff[x + 1] - L.heoff[x]);
@@ -1561,7 +1322,7 @@ extern "C" cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t s
         const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
         int per_sm = 0;
         const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)batch_kernel(fp32, b->lv[level].col16, shape->lanes_per_row), threads_for_gpc(*shape),
+            &per_sm, (const void *)batch_kernel(fp32, b->lv[level].lay.col16, shape->lanes_per_row), threads_for_gpc(*shape),
             (size_t)b->lv[level].smem_group * shape->graphs_per_cta);
         if (e != cudaSuccess || per_sm < 1) st = CMG_ERR_INVALID_ARG;
     }
@@ -1591,7 +1352,7 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
         int per_sm = 0;
         const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
         CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)batch_kernel(fp32, V.col16, sh.lanes_per_row), threads_for_gpc(sh),
+            &per_sm, (const void *)batch_kernel(fp32, V.lay.col16, sh.lanes_per_row), threads_for_gpc(sh),
             (size_t)V.smem_group * sh.graphs_per_cta));
         if (per_sm < 1) {
             *ms = 1e30f;

@@ -51,6 +51,38 @@ cmg_status_t load_level0(int64_t n, const int64_t *row_ptr, const int32_t *col, 
 // w32[k] = (float)w[k].
 cmg_status_t launch_to_float(long long m, const double *w, float *w32, cudaStream_t s);
 
+// Sweep layout of a level, per graph (built at setup): rows renumbered by
+// decreasing degree (stable); the rows with more than kHeavy entries come
+// first and keep CSR form ("heavy" rows), the others form slices of 32 rows
+// whose entries are interleaved -- entry k of the slice's row l sits at
+// slice_offset + 32 k + l, shorter rows padded with weight 0 -- so a warp
+// reads a slice with coalesced loads that do not depend on each other.
+// Columns are renumbered local ids (16-bit when every graph of the level
+// has at most 65536 vertices).  meta of a graph: the entry offsets (local to
+// the graph) of its h heavy rows, then of its nsl slices, then the end.
+constexpr int kHeavy = 32;
+
+struct SweepLayout {
+    uint32_t *perm = nullptr;   // new position -> original vertex (union numbering)
+    int *inv = nullptr;         // original vertex -> new position
+    int *heavy = nullptr;       // [G] heavy rows per graph
+    int *eoff = nullptr;        // [G+1] first layout entry of each graph
+    int *moff = nullptr;        // [G+1] first meta word of each graph
+    int *meta = nullptr;        // per graph: offsets of h heavy rows, nsl slices, end
+    void *bcol = nullptr;       // uint16 (col16) or int32 local columns
+    void *bw = nullptr;         // weights in the sweep precision
+    int col16 = 1;
+    long long entries = 0;
+    std::vector<int> hecnt, hmcnt, hheavy;   // per graph, host copies
+};
+// Builds the layout of the N rows of a level holding G graphs at union
+// offsets voff (device, G+1; host copy hvoff) from the level's CSR; fp32
+// selects float weights.  Adds its device bytes to *bytes (nullable).
+cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &hvoff, int N,
+                                const int *rp, const int *col, const double *w, int fp32,
+                                SweepLayout *L, size_t *bytes, cudaStream_t s);
+void free_sweep_layout(SweepLayout &L, cudaStream_t s);
+
 // Bits needed for the ids 0..c-1 (at least 1).
 inline int bits_for(int c) {
     int b = 1;
@@ -109,6 +141,9 @@ struct PiLevel {
     const int *tile_row; // row tiles of the sweep kernel (nullptr: built on demand)
     int ntiles;
     long long sell_nnz;  // SELL-32 size for the shared-memory kernel (0: unknown)
+    // sweep layout (one graph) for the slice kernel, or nullptr; with a layout
+    // the level's iterates are stored in the layout's row order
+    const SweepLayout *lay;
 };
 
 // SELL-32 size of a CSR level (sum over 32-row slices of 32 x longest row);
@@ -142,6 +177,7 @@ struct PiRun {
     const void *coarse_bufs[3];
     const PiResult *coarse_res;
     const int *coarse_agg;           // agg of this level onto the coarse level
+    const int *coarse_inv;           // the coarse level's layout order (nullptr: natural)
     const double *x_init;
     void *bufs[3];
     double *gd;
@@ -167,6 +203,9 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s,
 //   - if `sign`: scale u so that its largest-|u_i| entry (lowest index on
 //     ties) is positive;
 //   - out2[0] = u^T L u / u^T u, out2[1] = ||(L - out2[0] I) u|| / ||u||.
+// True when the shared-memory kernel can hold the whole level.
+bool small_level_fits(const PiLevel &lv, int fp32);
+
 cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const PiResult *res,
                       double *u, int sign, int fresh, double *out2, GridSync *gs, cudaStream_t s,
                       const PiWorkspace *ws = nullptr);

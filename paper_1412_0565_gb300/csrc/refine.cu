@@ -95,6 +95,13 @@ struct PiArgs {
     ff *partials;           // [2][gridDim.x][3] (tiled kernel)
     float zero_tol2;        // (64 eps)^2 of the sweep precision
     long long sell_nnz;     // SELL-32 size of the level (0: unknown)
+    const int *cinvp;       // coarse level's layout order (start = 1), or nullptr
+    // slice kernel: the level's sweep layout (rows in layout order)
+    const int *perm;
+    int lay_h, lay_nsl;
+    const int *lay_meta;
+    const void *lay_col;
+    const void *lay_w;
 };
 
 
@@ -104,7 +111,10 @@ template <typename T>
 __device__ __forceinline__ double start_value(const PiArgs &a, int i, const T *cb, double cmu,
                                               double cinv) {
     if (a.start == 0) return gaussian_entry(a.seed, i);
-    if (a.start == 1) return ((double)cb[a.agg[i]] - cmu) * cinv;
+    if (a.start == 1) {
+        const int c = a.agg[i];
+        return ((double)cb[a.cinvp ? a.cinvp[c] : c] - cmu) * cinv;
+    }
     return a.x_init[i];
 }
 
@@ -502,6 +512,230 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
     if (warp == 0) {
         if (exit_kind == 2 && !no_sweeps) {
             // the last sweep s ended the loop by count: reduce it now
+            Part q = part_zero();
+            const ff *base = a.partials + (size_t)(s & 1) * gridDim.x * 3;
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const ff *src = base + (size_t)b * 3;
+                Part t;
+                t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                q = part_add(q, t);
+            }
+            q = warp_sum_part(q);
+            ctrl_step(a, s, q, c, nullptr, true);
+        }
+        if (blockIdx.x == 0 && lane == 0) {
+            const int rs = c.res_sweep;
+            const int rb = c.zero ? (rs - 1) % 3 : rs % 3;
+            write_result(a, c, rb, (rs + 2) % 3);
+        }
+    }
+}
+
+// ================================================================== slice kernel
+// Large levels with a sweep layout (rows renumbered by decreasing degree;
+// heavy rows in CSR form, the rest in 32-row slices with interleaved entries):
+// cooperative persistent kernel with the control warp of k_power_tiled.  A
+// row warp takes a heavy row (32 lanes over its entries) or a slice (one lane
+// per row; entry k of the slice's rows is one coalesced load), so the loads of
+// a sweep do not wait on one another and no CTA barrier is needed inside a
+// sweep.  The iterates are stored in layout order.
+template <typename T, typename IDX>
+__global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSync *gs) {
+    __shared__ Part s_pw[kTileThreads / 32];
+    __shared__ Slot s_slot[2];
+    const int n = a.n;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    T *const ring0 = (T *)a.buf[0], *const ring1 = (T *)a.buf[1], *const ring2 = (T *)a.buf[2];
+    const bool fp64 = sizeof(T) == 8;
+    const T g = (T)a.g;
+    const float inv_gf = 1.0f / (float)a.g;
+    const double inv_gd = 1.0 / a.g;
+    const int h = a.lay_h, nsl = a.lay_nsl;
+    const int *__restrict__ M = a.lay_meta;
+    const int *__restrict__ SO = M + h;
+    const IDX *__restrict__ C = reinterpret_cast<const IDX *>(a.lay_col);
+    const T *__restrict__ W = reinterpret_cast<const T *>(a.lay_w);
+    // work of this CTA: a contiguous range of slices; heavy rows go round robin
+    const int sb = (int)((long long)nsl * blockIdx.x / gridDim.x);
+    const int se = (int)((long long)nsl * (blockIdx.x + 1) / gridDim.x);
+    const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
+    const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
+
+    // ---------------------------------------------------------- start phase
+    {
+        const T *cb = nullptr;
+        double cmu = 0.0, cinv = 0.0;
+        if (a.start == 1) {
+            cb = (const T *)a.cbuf[a.cres->buf];
+            cmu = a.cres->mu;
+            cinv = a.cres->inv_s;
+        }
+        Part acc = part_zero();
+        for (int p = r0 + tid; p < r1; p += blockDim.x) {
+            const int old = a.perm[p];
+            const T xt = (T)start_value<T>(a, old, cb, cmu, cinv);
+            ring0[p] = xt;
+            if (fp64) {
+                double d = 0.0;
+                for (int e = __ldg(a.rp + old), e1 = __ldg(a.rp + old + 1); e < e1; e++) d += __ldg(a.w + e);
+                a.gd[p] = a.g - d;
+            }
+            const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
+            acc.A = ff_add(acc.A, v);
+            acc.B = ff_add(acc.B, ff_mul(v, v));
+        }
+        Part p = warp_sum_part(acc);
+        if (lane == 0) s_pw[warp] = p;
+        __syncthreads();
+        if (warp == 0) {
+            Part q = (lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + (size_t)blockIdx.x * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+    }
+    if (!grid_sync(gs)) return;
+    Ctl c;
+    if (warp == 0) {
+        Part q = part_zero();
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const ff *src = a.partials + (size_t)b * 3;
+            Part t;
+            t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+            t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+            t.C = ff_zero();
+            q = part_add(q, t);
+        }
+        q = warp_sum_part(q);
+        const double mu0 = to_d(q.A) / (double)n;
+        double ss0 = to_d(q.B) - (double)n * mu0 * mu0;
+        if (ss0 < 0.0) ss0 = 0.0;
+        const int e0 = start_exponent(ss0);
+        ctl_init(c, a, mu0, ss0, e0);
+        if (lane == 0) {
+            s_slot[1] = slot_make(ff_from_double(mu0), e0);
+            s_slot[0] = slot_make(ff_zero(), 0);
+        }
+    }
+    __syncthreads();
+
+    const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
+    int s = 0;
+    int exit_kind = no_sweeps ? 2 : 0;
+    const int rw = warp - 1, nrw = (int)(blockDim.x >> 5) - 1;            // row warps of this CTA
+    const int gw = blockIdx.x * nrw + rw, ngw = (int)gridDim.x * nrw;     // over the grid
+    while (!no_sweeps) {
+        const Slot sl = s_slot[(s + 1) & 1];
+        if (sl.stop) {
+            exit_kind = 1;
+            break;
+        }
+        if ((a.mode == 1 && s >= a.k_fixed) || (a.mode == 0 && s >= a.max_sweeps)) {
+            exit_kind = 2;
+            break;
+        }
+        const T *x = pick3<T *>(ring0, ring1, ring2, s % 3);
+        T *y = pick3<T *>(ring0, ring1, ring2, (s + 1) % 3);
+        if (warp == 0) {
+            if (s >= 1) {
+                Part q = part_zero();
+                const ff *base = a.partials + (size_t)(s & 1) * gridDim.x * 3;
+                for (int b = lane; b < (int)gridDim.x; b += 32) {
+                    const ff *src = base + (size_t)b * 3;
+                    Part t;
+                    t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                    t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                    t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                    q = part_add(q, t);
+                }
+                q = warp_sum_part(q);
+                Slot nx;
+                ctrl_step(a, s, q, c, &nx, false);
+                if (lane == 0) s_slot[s & 1] = nx;
+            }
+        } else {
+            const T m = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
+            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
+            const T gm = g * m;
+            Acc<T> acc;
+            acc.reset();
+            auto finish = [&](int i, T xi, T ac) {
+                T yv;
+                if (fp64) yv = (T)((fma(a.gd[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
+                else yv = (g * (xi - m) - ac) * sig;
+                y[i] = yv;
+                acc.add(yv, xi);
+            };
+            // heavy rows: a warp per row
+            for (int r = gw; r < h; r += ngw) {
+                const T xi = LDXG(x + r);
+                T ac = (T)0;
+                for (int f = M[r] + lane, f1 = M[r + 1]; f < f1; f += 32) {
+                    const T xj = LDXG(x + C[f]);
+                    if (fp64) ac = fma(W[f], xj, ac);
+                    else ac += W[f] * (xi - xj);
+                }
+                ac = warp_sum(ac);
+                if (lane == 0) finish(r, xi, ac);
+            }
+            // slices: a lane per row
+            for (int q = sb + rw; q < se; q += nrw) {
+                const int i = h + 32 * q + lane;
+                const int so = SO[q] + lane, wd = (SO[q + 1] - SO[q]) >> 5;
+                const T xi = (i < n) ? LDXG(x + i) : (T)0;
+                T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
+                int k = 0;
+                for (; k + 3 < wd; k += 4) {
+                    const int f = so + 32 * k;
+                    const int c0 = C[f], c1 = C[f + 32], c2 = C[f + 64], c3 = C[f + 96];
+                    const T w0 = W[f], w1 = W[f + 32], w2 = W[f + 64], w3 = W[f + 96];
+                    const T x0 = LDXG(x + c0), x1 = LDXG(x + c1), x2 = LDXG(x + c2), x3 = LDXG(x + c3);
+                    if (fp64) {
+                        a0 = fma(w0, x0, a0);
+                        a1 = fma(w1, x1, a1);
+                        a2 = fma(w2, x2, a2);
+                        a3 = fma(w3, x3, a3);
+                    } else {
+                        a0 += w0 * (xi - x0);
+                        a1 += w1 * (xi - x1);
+                        a2 += w2 * (xi - x2);
+                        a3 += w3 * (xi - x3);
+                    }
+                }
+                for (; k < wd; k++) {
+                    const int f = so + 32 * k;
+                    const T xv = LDXG(x + C[f]);
+                    if (fp64) a0 = fma(W[f], xv, a0);
+                    else a0 += W[f] * (xi - xv);
+                }
+                if (i < n) finish(i, xi, (a0 + a1) + (a2 + a3));
+            }
+            Part p = warp_sum_part(acc.get());
+            if (lane == 0) s_pw[warp] = p;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            Part q = (lane >= 1 && lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + ((size_t)((s + 1) & 1) * gridDim.x + blockIdx.x) * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+        if (!grid_sync(gs)) return;
+        s++;
+    }
+    // ---------------------------------------------------------- result
+    if (warp == 0) {
+        if (exit_kind == 2 && !no_sweeps) {
             Part q = part_zero();
             const ff *base = a.partials + (size_t)(s & 1) * gridDim.x * 3;
             for (int b = lane; b < (int)gridDim.x; b += 32) {
@@ -922,6 +1156,11 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.partials = nullptr;
     a.zero_tol2 = run.fp32 ? kZeroTol2_32 : kZeroTol2_64;
     a.sell_nnz = lv.sell_nnz;
+    a.cinvp = run.coarse_inv;
+    a.perm = nullptr;
+    a.lay_h = a.lay_nsl = 0;
+    a.lay_meta = nullptr;
+    a.lay_col = a.lay_w = nullptr;
     void *args[] = {&a, &gs};
     if (small_level_fits(lv, run.fp32)) {
         const int G = small_lanes(lv.n, lv.nnz, run.fp32);
@@ -931,6 +1170,33 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
         return coop_launch(kern, 1, small_threads(lv.n, G), smem, s, args, gs);
     }
     if (!run.fp32 && !run.gd) return CMG_ERR_INVALID_ARG;
+    if (lv.lay) {
+        // slice kernel over the level's sweep layout (one graph)
+        const SweepLayout &L = *lv.lay;
+        a.perm = reinterpret_cast<const int *>(L.perm);
+        a.lay_h = L.hheavy[0];
+        a.lay_nsl = (lv.n - a.lay_h + 31) / 32;
+        a.lay_meta = L.meta;
+        a.lay_col = L.bcol;
+        a.lay_w = L.bw;
+        const void *kern;
+        if (run.fp32) kern = L.col16 ? (const void *)k_power_sell<float, uint16_t> : (const void *)k_power_sell<float, int>;
+        else kern = L.col16 ? (const void *)k_power_sell<double, uint16_t> : (const void *)k_power_sell<double, int>;
+        int maxb = 0;
+        CMG_TRY(coop_max_blocks(kern, kTileThreads, 0, &maxb));
+        const int row_warps = kTileThreads / 32 - 1;
+        const long long tasks = (long long)a.lay_nsl + a.lay_h;
+        const int blocks = (int)std::max<long long>(1, std::min<long long>(maxb, (tasks + row_warps - 1) / row_warps));
+        double *partials;
+        if (ws) {
+            if (2 * blocks * 3 > ws->partials_cap) return CMG_ERR_TOO_LARGE;
+            partials = ws->partials;
+        } else {
+            CMG_TRY(scr.get(&partials, (size_t)2 * blocks * 3));
+        }
+        a.partials = reinterpret_cast<ff *>(partials);
+        return coop_launch(kern, blocks, kTileThreads, 0, s, args, gs);
+    }
     if (!a.tile_row) {
         int *tr;
         if (ws) {
@@ -1043,6 +1309,7 @@ struct FinArgs {
     double *out;       // [2]: lambda, residual
     int sign;          // apply the canonical sign
     int fresh;         // u already holds the vector (skip the vector phase)
+    const int *inv;    // the iterates are in layout order: row i is at inv[i] (nullptr: natural)
 };
 
 // (|v|, index) order of the sign rule: larger magnitude first, lower index on ties.
@@ -1076,10 +1343,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinArgs a, GridSync *g
                 const int i = base;
                 double acc = 0.0, xi = 0.0;
                 if (i < r1) {
-                    xi = ((double)x[i] - r.mu_prev) * r.inv_s_prev;
+                    xi = ((double)x[a.inv ? a.inv[i] : i] - r.mu_prev) * r.inv_s_prev;
                     const int e1 = __ldg(a.rp + i + 1);
                     for (int e = __ldg(a.rp + i) + lane; e < e1; e += G) {
-                        const double xj = ((double)x[__ldg(a.col + e)] - r.mu_prev) * r.inv_s_prev;
+                        const int j = __ldg(a.col + e);
+                        const double xj = ((double)x[a.inv ? a.inv[j] : j] - r.mu_prev) * r.inv_s_prev;
                         acc += __ldg(a.w + e) * (xi - xj);
                     }
                 }
@@ -1099,10 +1367,11 @@ __global__ void __launch_bounds__(kFinThreads) k_finalize(FinArgs a, GridSync *g
         } else if (a.fp32) {
             const float *y = (const float *)a.buf[r.buf];
             for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
-                a.u[i] = ((double)y[i] - r.mu) * r.inv_s;
+                a.u[i] = ((double)y[a.inv ? a.inv[i] : i] - r.mu) * r.inv_s;
         } else {
             const double *y = (const double *)a.buf[r.buf];
-            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x) a.u[i] = (y[i] - r.mu) * r.inv_s;
+            for (int i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+                a.u[i] = (y[a.inv ? a.inv[i] : i] - r.mu) * r.inv_s;
         }
     }
     // ---- canonical sign: the entry of largest |u_i| (lowest index on ties) is
@@ -1264,6 +1533,7 @@ cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const Pi
     a.out = out2;
     a.sign = sign;
     a.fresh = fresh;
+    a.inv = lv.lay ? lv.lay->inv : nullptr;
     void *args[] = {&a, &gs};
     return coop_launch(kern, blocks, kFinThreads, 0, s, args, gs);
 }
