@@ -116,6 +116,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+PROFILE = os.path.join(ROOT, "profiles", "k_power_sell_f32_grid3d_100_level0.md")
+PROFILED_SOURCES = [os.path.join(ROOT, "paper_1412_0565_gb300", "csrc", f)
+                    for f in ("refine.cu", "pi_common.cuh", "ffloat.cuh")]
+
+
+def profiled_traffic():
+    """DRAM bytes per level-0 launch from the committed ncu summary, or None
+    when the kernel sources changed since that capture."""
+    import hashlib
+    try:
+        text = open(PROFILE).read()
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in PROFILED_SOURCES)).hexdigest()[:16]
+        fields = dict(line.strip("- ").split(": ", 1) for line in text.splitlines()
+                      if line.startswith("- ") and ": " in line)
+        if fields.get("kernel_source_sha256_16") != h:
+            return None, "kernel changed since the ncu capture"
+        return int(fields["traffic_bytes_per_launch"]), "dram read+write per launch, ncu (profiles/)"
+    except Exception as e:  # missing or malformed summary
+        return None, f"no ncu summary ({type(e).__name__})"
+
+
 def cpu_info():
     model = ""
     try:
@@ -266,9 +287,11 @@ def run_gpu(args):
         hbm_peak = 6800.0
     ms0, by0, tot_b, tot_ms, st32 = roofline(r32, True)
     achieved0 = by0 / (ms0 * 1e-3) / 1e9
-    roof = {"bound": "hbm", "kernel": "k_power_tiled<float>, level-0 launch",
+    traffic, traffic_note = profiled_traffic()
+    roof = {"bound": "hbm", "kernel": "k_power_sell<float, int>, level-0 launch",
             "achieved": achieved0, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-            "frac": achieved0 / hbm_peak, "traffic": None, "bytes_per_launch": by0,
+            "frac": achieved0 / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
+            "bytes_per_launch": by0,
             "launch_ms": ms0, "sweeps_per_launch": st32["sweeps"][0],
             "all_levels": {"bytes": tot_b, "ms": tot_ms, "achieved": tot_b / (tot_ms * 1e-3) / 1e9}}
     ms0_64, by0_64, tot_b64, tot_ms64, st64 = roofline(r64, False)
@@ -531,6 +554,20 @@ def run_serving(args):
     rel = np.abs(lam_by["fp32"] - lam_by["fp64_plain"]) / np.abs(lam_by["fp64_plain"])
     out["fp32_vs_fp64_lambda2_rel"] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
                                        "note": "tolerance mode (sweep counts may differ)"}
+    # precision alone on the serving graphs: FP32 sweeps replaying the FP64
+    # solve's per-level sweep counts
+    lam_rel, ang = [], []
+    for g in graphs[:args.serve_replay_sample]:
+        u64, l64, st64 = cmg.fiedler(*g, seed=1412, precision="fp64")
+        u32, l32, _ = cmg.fiedler(*g, seed=1412, precision="fp32", schedule="replay",
+                                  replay_sweeps=st64["sweeps"])
+        lam_rel.append(abs(l32 - l64) / abs(l64))
+        c = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
+        ang.append(float(np.arccos(min(1.0, c))))
+    out["fp32_vs_fp64_replay"] = {"graphs": len(lam_rel), "lambda2_rel_max": max(lam_rel),
+                                  "angle_max": max(ang),
+                                  "within_1e-6_and_1e-4": int(sum((r <= 1e-6) and (a <= 1e-4)
+                                                                  for r, a in zip(lam_rel, ang)))}
     return out
 
 
@@ -548,6 +585,7 @@ def main():
     ap.add_argument("--batch-plain-sample", type=int, default=32)
     ap.add_argument("--serve-graphs", type=int, default=48)
     ap.add_argument("--serve-requests", type=int, default=160)
+    ap.add_argument("--serve-replay-sample", type=int, default=16)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

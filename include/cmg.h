@@ -240,8 +240,9 @@ cmg_status_t cmg_batch_set_replay(cmg_batch_t b, const int32_t *sweeps);
 
 /* Launch shape of a union level's power-iteration kernel: `threads_per_graph`
  * threads (32..1024, a multiple of 32) work on one graph at a time,
- * `lanes_per_row` (1, 2, 4, 8, 16 or 32) of them on one row; a CTA holds
- * `graphs_per_cta` such groups (tpg * gpc <= 1024; gpc <= 15 unless
+ * `lanes_per_row` (1, 2, 4, 8, 16 or 32) of them on each row with more than
+ * 32 entries (shorter rows take one lane each, 32 rows per warp); a CTA
+ * holds `graphs_per_cta` such groups (tpg * gpc <= 1024; gpc <= 15 unless
  * tpg = 32); `stage_csr` = 1 lets a group copy its graph's CSR into shared
  * memory when it fits.  cmg_batch_config reads or sets one level's shape
  * (set = 0 reads into the pointers, 1 writes them); cmg_batch_autotune times
@@ -285,8 +286,11 @@ cmg_status_t cmg_batch_free(cmg_batch_t b);
  * (warm); a graph with n > batch_max_n is set up with cmg_setup, solved and
  * (keep_resident) kept; every pending request for a smaller graph without a
  * hierarchy, up to max_batch, joins one batched job (cmg_setup_batch +
- * cmg_fiedler_batch), so requests arriving while others run are admitted
- * together as soon as a worker and memory free up.  Pending requests are
+ * cmg_fiedler_batch) when at least min_batch of them are pending (a batched
+ * job gives each graph a group of threads, which pays only when many graphs
+ * fill the GPU; fewer run alone, with the whole GPU each), so requests
+ * arriving while others run are admitted together as soon as a worker and
+ * memory free up.  Pending requests are
  * taken first-fit in arrival order.  All requests use the server's options.
  * ---------------------------------------------------------------------- */
 typedef struct cmg_server_s *cmg_server_t;
@@ -298,7 +302,9 @@ typedef struct cmg_server_config {
     uint64_t mem_budget;   /* device bytes for jobs and resident hierarchies;
                               0 = 80% of the free device memory at creation          */
     int32_t keep_resident; /* keep single-form hierarchies after their solve (1)      */
-    int32_t reserved;      /* must be 0                                               */
+    int32_t min_batch;     /* batch small graphs only when at least this many cold
+                              small requests are pending; fewer run alone (32).
+                              0 selects the default                                  */
 } cmg_server_config_t;
 
 typedef struct cmg_request {
@@ -318,7 +324,8 @@ typedef struct cmg_server_stats {
     uint64_t budget_bytes;
 } cmg_server_stats_t;
 
-/* workers 4, max_batch 256, batch_max_n 50000, mem_budget 0, keep_resident 1. */
+/* workers 4, max_batch 256, batch_max_n 50000, mem_budget 0, keep_resident 1,
+ * min_batch 32. */
 cmg_status_t cmg_server_config_default(cmg_server_config_t *cfg);
 /* Starts the workers on the current device.  opts: NULL = defaults
  * (options.timing must be 0).  Errors: INVALID_ARG, CUDA. */

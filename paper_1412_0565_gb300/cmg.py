@@ -94,7 +94,7 @@ class BatchShape(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("workers", C.c_int32), ("max_batch", C.c_int32), ("batch_max_n", C.c_int64),
-                ("mem_budget", C.c_uint64), ("keep_resident", C.c_int32), ("reserved", C.c_int32)]
+                ("mem_budget", C.c_uint64), ("keep_resident", C.c_int32), ("min_batch", C.c_int32)]
 
 
 class Request(C.Structure):
@@ -485,12 +485,12 @@ class Server:
     submit requests, wait for results.  Graph arrays are kept alive here."""
 
     def __init__(self, *, workers=4, max_batch=256, batch_max_n=50000, mem_budget=0,
-                 keep_resident=1, opts: Options | None = None, **kw):
+                 keep_resident=1, min_batch=32, opts: Options | None = None, **kw):
         lib = load()
         cfg = ServerConfig()
         _check(lib.cmg_server_config_default(C.byref(cfg)), "server_config")
         cfg.workers, cfg.max_batch, cfg.batch_max_n = workers, max_batch, batch_max_n
-        cfg.mem_budget, cfg.keep_resident = mem_budget, keep_resident
+        cfg.mem_budget, cfg.keep_resident, cfg.min_batch = mem_budget, keep_resident, min_batch
         self.opts = opts if opts is not None else options(**kw)
         s = C.c_void_p()
         self._s = None

@@ -99,7 +99,7 @@ __global__ void k_batch_check(int n, int G, const int *__restrict__ voff, const 
 constexpr int kGroupHeader = 4096;   // per-group control area in shared memory
 constexpr int kOffDred = 2 * 32 * (int)sizeof(Part);
 constexpr int kOffInt = kOffDred + 32 * 4 * (int)sizeof(double);
-constexpr int kBatchMaxThreads = 512;
+constexpr int kBatchMaxThreads = 1024;
 static_assert(kOffInt + 64 <= kGroupHeader, "group header too small");
 
 
@@ -198,16 +198,8 @@ __device__ __forceinline__ bool sign_better(double v, int i, double bv, int bi) 
     return v > bv || (v == bv && i < bi);
 }
 
-// One sweep's contribution of row i: FP32 edge form sum w (x_i - x_j), FP64
-// degree form sum w x_j.
-template <typename T>
-__device__ __forceinline__ T edge_term(T acc, T w, T xi, T xj) {
-    if (sizeof(T) == 8) return fma(w, xj, acc);
-    return acc + w * (xi - xj);
-}
-
 template <typename T, typename IDX, int G>
-__global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a) {
+__global__ void __launch_bounds__(kBatchMaxThreads, 1) k_batch_pi(BatchPiArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr bool fp64 = sizeof(T) == 8;
     const int tg = a.tg;
@@ -379,8 +371,8 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
                 T ac = (T)0, xi = (T)0;
                 if (i < h) {
                     xi = x[i];
-                    for (int f = M[i] + rl, f1 = M[i + 1]; f < f1; f += G)
-                        ac = edge_term<T>(ac, W[f], xi, x[C[f]]);
+                    ac = row_sum_grouped<T, IDX>(C, W, M[i] + rl, M[i + 1], G, xi,
+                                                 [&](int c) { return x[c]; });
                 }
                 ac = group_sum<G>(ac);
                 if (i < h && rl == 0) finish_row(i, xi, ac);
@@ -390,22 +382,9 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
                 const int i = h + 32 * sl + lane;
                 const int so = SO[sl] + lane, wd = (SO[sl + 1] - SO[sl]) >> 5;
                 const T xi = (i < n) ? x[i] : (T)0;
-                T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-                int kk = 0;
-                for (; kk + 3 < wd; kk += 4) {
-                    const int f = so + 32 * kk;
-                    const int c0 = C[f], c1 = C[f + 32], c2 = C[f + 64], c3 = C[f + 96];
-                    const T w0 = W[f], w1 = W[f + 32], w2 = W[f + 64], w3 = W[f + 96];
-                    a0 = edge_term<T>(a0, w0, xi, x[c0]);
-                    a1 = edge_term<T>(a1, w1, xi, x[c1]);
-                    a2 = edge_term<T>(a2, w2, xi, x[c2]);
-                    a3 = edge_term<T>(a3, w3, xi, x[c3]);
-                }
-                for (; kk < wd; kk++) {
-                    const int f = so + 32 * kk;
-                    a0 = edge_term<T>(a0, W[f], xi, x[C[f]]);
-                }
-                if (i < n) finish_row(i, xi, (a0 + a1) + (a2 + a3));
+                const T ac = row_sum_grouped<T, IDX>(C, W, so, so + 32 * wd, 32, xi,
+                                                     [&](int c) { return x[c]; });
+                if (i < n) finish_row(i, xi, ac);
             }
             const Part P = gsum_part<1>(acc.get(), s_part + 32 * ((s + 1) & 1), lane, wg, nwg, bid, tg);
             const ff mu1 = ff_mul(P.A, inv_n);
@@ -592,6 +571,61 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 2) k_batch_pi(BatchPiArgs a)
     }
 }
 
+// Queue order of a level by predicted work, longest first: the graph's
+// sweeps on the next coarser level (just solved) times its rows + entries on
+// this level; graphs without a coarser solve keep their size order after the
+// others.  One CTA, bitonic sort in shared memory (count <= kOrderMax).
+constexpr int kOrderMax = 8192;
+
+__global__ void __launch_bounds__(1024) k_order_level(int count, const int *__restrict__ list_in,
+                                                      const int *__restrict__ sweeps_coarse,
+                                                      const int *__restrict__ J, int level,
+                                                      const int *__restrict__ voff,
+                                                      const int *__restrict__ rp, int *__restrict__ list_out) {
+    extern __shared__ __align__(16) unsigned char order_smem[];
+    unsigned long long *key = reinterpret_cast<unsigned long long *>(order_smem);   // [m]
+    int m = 1;
+    while (m < count) m <<= 1;
+    int *val = reinterpret_cast<int *>(key + m);   // [m]
+    for (int t = threadIdx.x; t < m; t += blockDim.x) {
+        if (t < count) {
+            const int q = list_in[t];
+            const unsigned long long size =
+                (unsigned long long)(voff[q + 1] - voff[q]) + (unsigned long long)(rp[voff[q + 1]] - rp[voff[q]]);
+            const unsigned long long sw = (J[q] > level) ? (unsigned long long)max(sweeps_coarse[q], 1) : 0ull;
+            // work (48 bits) then the input position (ties keep the size order)
+            const unsigned long long work = min(sw * size, (1ull << 47) - 1);
+            key[t] = (work << 16) | (unsigned long long)(0xffff - min(t, 0xffff));
+            val[t] = q;
+        } else {
+            key[t] = 0ull;   // padding sorts last
+            val[t] = -1;
+        }
+    }
+    __syncthreads();
+    // bitonic sort, descending
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int t = threadIdx.x; t < m; t += blockDim.x) {
+                const int u = t ^ j;
+                if (u > t) {
+                    const bool desc = (t & k) == 0;
+                    const unsigned long long a = key[t], b = key[u];
+                    if (desc ? (a < b) : (a > b)) {
+                        key[t] = b;
+                        key[u] = a;
+                        const int tv = val[t];
+                        val[t] = val[u];
+                        val[u] = tv;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int t = threadIdx.x; t < count; t += blockDim.x) list_out[t] = val[t];
+}
+
 typedef void (*BatchKernel)(BatchPiArgs);
 
 template <typename T, typename IDX>
@@ -633,7 +667,9 @@ struct BLevel {
     std::vector<int> heoff;      // row_ptr at hvoff
     std::vector<double> hg;
     int *list = nullptr;         // graphs solved on this level, largest first
+    int *order = nullptr;        // the same graphs by predicted work (set per solve)
     int count = 0;
+    int kbig = 0;                // graphs of the level's big-graph launch
     long long max_vbytes = 0;    // largest graph on the list: vector bytes
     long long max_cbytes = 0;    //                            CSR bytes
     void *u = nullptr;           // normalised level result (levels > 0)
@@ -652,6 +688,7 @@ void free_blevel(BLevel &L, cudaStream_t s) {
     dev_free(L.voff, s);
     dev_free(L.gsh, s);
     dev_free(L.list, s);
+    dev_free(L.order, s);
     dev_free(L.u, s);
     dev_free(L.vscr, s);
     dev_free(L.gdscr, s);
@@ -684,6 +721,9 @@ struct cmg_batch_s {
     bool dirty = true;
     unsigned long long graph_kernels = 0;
     std::vector<double> level_ms;     // options.timing: device time per union level
+    cudaStream_t side = nullptr;      // second stream: the big-graph launch of a level
+    std::vector<cudaEvent_t> ev_fork, ev_join;
+    int *tune_replay = nullptr;       // autotuner: replayed sweep counts
     size_t bytes = 0;
 };
 
@@ -711,8 +751,12 @@ static void free_batch(cmg_batch_s *b) {
     dev_free(b->res, b->stream);
     dev_free(b->uf, b->stream);
     dev_free(b->replay, b->stream);
+    dev_free(b->tune_replay, b->stream);
     cudaStreamSynchronize(b->stream);
     if (b->cap) cudaStreamDestroy(b->cap);
+    if (b->side) cudaStreamDestroy(b->side);
+    for (cudaEvent_t e : b->ev_fork) cudaEventDestroy(e);
+    for (cudaEvent_t e : b->ev_join) cudaEventDestroy(e);
     cudaSetDevice(prev);
     delete b;
 }
@@ -740,6 +784,23 @@ static int group_smem(const BLevel &L, const cmg_batch_shape_t &sh, int max_opti
     return (int)((kGroupHeader + d) / 16 * 16);
 }
 
+
+// A level with enough graphs runs its largest-work graphs (a quarter of the
+// level, at most kBigGraphs) in a launch of their own, one 1024-thread group
+// per graph, so the graphs whose sweeps form the level's longest serial
+// chains get the most threads; the rest run concurrently in the level's
+// tuned shape.
+constexpr int kBigGraphs = 64;
+
+static cmg_batch_shape_t big_shape(const BLevel &L) {
+    cmg_batch_shape_t sh;
+    sh.threads_per_graph = kBatchMaxThreads;
+    sh.lanes_per_row = L.shape.lanes_per_row;
+    sh.graphs_per_cta = 1;
+    sh.stage_csr = 1;
+    return sh;
+}
+
 static cmg_batch_shape_t default_shape(const BLevel &L) {
     double avg_n = 0.0, avg_deg = 0.0;
     // per-graph sizes of the listed graphs are not kept on the host; the
@@ -764,7 +825,8 @@ static cmg_status_t level_workspace(cmg_batch_s *b, int j, cudaStream_t s) {
     DeviceInfo di;
     CMG_TRY(device_info(&di));
     L.smem_group = group_smem(L, L.shape, di.max_smem_optin);
-    if (L.max_vbytes > L.smem_group - kGroupHeader && !L.vscr) {
+    const int big_group = group_smem(L, big_shape(L), di.max_smem_optin);
+    if (L.max_vbytes > std::min(L.smem_group, big_group) - kGroupHeader && !L.vscr) {
         CMG_TRY(dev_alloc(&L.vscr, 2 * esz * (size_t)std::max(L.n, 1), s));
         b->bytes += 2 * esz * (size_t)L.n;
         if (!fp32) {
@@ -780,20 +842,23 @@ static cmg_status_t level_workspace(cmg_batch_s *b, int j, cudaStream_t s) {
     return CMG_OK;
 }
 
-static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_t s) {
+// One launch of level j's kernel over `count` graphs of `list` with the
+// given shape and queue counter.
+static cmg_status_t launch_part(cmg_batch_s *b, int j, int force_k, cudaStream_t s, const int *list,
+                                int count, int *queue, const cmg_batch_shape_t &shape, int smem_group) {
     BLevel &L = b->lv[j];
-    if (L.count == 0) return CMG_OK;
+    if (count <= 0) return CMG_OK;
     const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
     const cmg_options_t &o = b->opts;
-    BatchKernel kern = batch_kernel(fp32, L.lay.col16, L.shape.lanes_per_row);
-    const int threads = threads_for_gpc(L.shape);
-    const int smem = L.smem_group * L.shape.graphs_per_cta;
+    BatchKernel kern = batch_kernel(fp32, L.lay.col16, shape.lanes_per_row);
+    const int threads = threads_for_gpc(shape);
+    const int smem = smem_group * shape.graphs_per_cta;
     int per_sm = 0;
     CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)kern, threads, smem));
     if (per_sm < 1) return CMG_ERR_INVALID_ARG;
     DeviceInfo di;
     CMG_TRY(device_info(&di));
-    const int blocks = std::max(1, std::min(div_up(L.count, L.shape.graphs_per_cta), per_sm * di.sms));
+    const int blocks = std::max(1, std::min(div_up(count, shape.graphs_per_cta), per_sm * di.sms));
     BatchPiArgs a;
     memset(&a, 0, sizeof(a));
     a.level = j;
@@ -810,9 +875,9 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     a.bw = L.lay.bw;
     a.voff = L.voff;
     a.gsh = L.gsh;
-    a.list = L.list;
-    a.count = L.count;
-    a.queue = b->queue + j;
+    a.list = list;
+    a.count = count;
+    a.queue = queue;
     a.J = b->dJ;
     a.agg = L.agg;
     a.uc = (j + 1 < (int)b->lv.size()) ? b->lv[j + 1].u : nullptr;
@@ -820,12 +885,12 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     a.uf = b->uf;
     a.vscr = L.vscr;
     a.gdscr = L.gdscr;
-    a.tg = L.shape.threads_per_graph;
-    a.smem_group = L.smem_group;
-    a.stage = L.shape.stage_csr;
+    a.tg = shape.threads_per_graph;
+    a.smem_group = smem_group;
+    a.stage = shape.stage_csr;
     a.fixed = o.schedule == CMG_SCHEDULE_FIXED;
     a.k_fixed = (int)ceil((double)o.k0 * pow(o.beta, (double)j));
-    a.replay = (o.schedule == CMG_SCHEDULE_REPLAY) ? b->replay : nullptr;
+    a.replay = b->tune_replay ? b->tune_replay : ((o.schedule == CMG_SCHEDULE_REPLAY) ? b->replay : nullptr);
     a.force_k = force_k;
     a.max_sweeps = o.max_sweeps;
     a.max_sweeps_coarsest = o.max_sweeps_coarsest;
@@ -841,10 +906,54 @@ static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_
     return launch_status();
 }
 
+// All launches of level j.  With a work order (use_order) and big graphs on
+// the level, the first kbig graphs of the order run in their own launch on
+// the side stream while the rest run on `s` (fork/join through events, so the
+// pair is also captured as two parallel graph branches).
+static cmg_status_t launch_level(cmg_batch_s *b, int j, int force_k, cudaStream_t s,
+                                 bool use_order = false) {
+    BLevel &L = b->lv[j];
+    if (L.count == 0) return CMG_OK;
+    const int *list = (use_order && L.order) ? L.order : L.list;
+    const int kbig = use_order ? std::min(L.kbig, L.count) : 0;
+    if (kbig == 0)
+        return launch_part(b, j, force_k, s, list, L.count, b->queue + 2 * j, L.shape, L.smem_group);
+    CMG_CUDA(cudaEventRecord(b->ev_fork[j], s));
+    CMG_CUDA(cudaStreamWaitEvent(b->side, b->ev_fork[j], 0));
+    DeviceInfo di;
+    CMG_TRY(device_info(&di));
+    const cmg_batch_shape_t bs = big_shape(L);
+    CMG_TRY(launch_part(b, j, force_k, b->side, list, kbig, b->queue + 2 * j + 1, bs,
+                        group_smem(L, bs, di.max_smem_optin)));
+    CMG_TRY(launch_part(b, j, force_k, s, list + kbig, L.count - kbig, b->queue + 2 * j, L.shape,
+                        L.smem_group));
+    CMG_CUDA(cudaEventRecord(b->ev_join[j], b->side));
+    CMG_CUDA(cudaStreamWaitEvent(s, b->ev_join[j], 0));
+    return CMG_OK;
+}
+
+// Orders level j's queue by predicted work (see k_order_level).
+static cmg_status_t order_level(cmg_batch_s *b, int j, cudaStream_t s, bool *ordered) {
+    BLevel &L = b->lv[j];
+    *ordered = false;
+    if (j + 1 >= (int)b->lv.size() || L.count < 2 || L.count > kOrderMax) return CMG_OK;
+    int m = 1;
+    while (m < L.count) m <<= 1;
+    k_order_level<<<1, 1024, (size_t)m * 12, s>>>(L.count, L.list, b->sweeps + (size_t)(j + 1) * b->G,
+                                                 b->dJ, j, L.voff, L.rp, L.order);
+    CMG_TRY(launch_status());
+    *ordered = true;
+    return CMG_OK;
+}
+
 static cmg_status_t enqueue_solve(cmg_batch_s *b, int force_k, cudaStream_t s) {
     const int L = (int)b->lv.size();
-    CMG_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int) * L, s));
-    for (int j = L - 1; j >= 0; j--) CMG_TRY(launch_level(b, j, force_k, s));
+    CMG_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int) * 2 * L, s));
+    for (int j = L - 1; j >= 0; j--) {
+        bool ordered = false;
+        if (force_k < 0) CMG_TRY(order_level(b, j, s, &ordered));
+        CMG_TRY(launch_level(b, j, force_k, s, ordered));
+    }
     return CMG_OK;
 }
 
@@ -878,7 +987,9 @@ static cmg_status_t build_lists(cmg_batch_s *b, cudaStream_t s) {
             return wx > wy;
         });
         L.count = (int)ids.size();
+        L.kbig = (L.count >= 16) ? std::min(kBigGraphs, L.count / 4) : 0;
         CMG_TRY(dev_alloc_n(&L.list, std::max<size_t>(ids.size(), 1), s));
+        CMG_TRY(dev_alloc_n(&L.order, std::max<size_t>(ids.size(), 1), s));
         if (!ids.empty())
             CMG_CUDA(cudaMemcpyAsync(L.list, ids.data(), sizeof(int) * ids.size(), cudaMemcpyHostToDevice, s));
         b->bytes += sizeof(int) * ids.size();
@@ -1056,7 +1167,7 @@ static cmg_status_t build_batch(cmg_batch_s *b, const int64_t *offs, const int64
     }
     CMG_TRY(dev_alloc_n(&b->dJ, (size_t)G, s));
     CMG_CUDA(cudaMemcpyAsync(b->dJ, b->J.data(), sizeof(int) * G, cudaMemcpyHostToDevice, s));
-    CMG_TRY(dev_alloc_n(&b->queue, (size_t)L, s));
+    CMG_TRY(dev_alloc_n(&b->queue, (size_t)2 * L, s));
     CMG_TRY(dev_alloc_n(&b->sweeps, (size_t)L * G, s));
     CMG_TRY(dev_alloc_n(&b->flags, (size_t)L * G, s));
     CMG_TRY(dev_alloc_n(&b->cosv, (size_t)L * G, s));
@@ -1077,6 +1188,13 @@ static cmg_status_t build_batch(cmg_batch_s *b, const int64_t *offs, const int64
     }
     b->bytes = bytes;
     CMG_TRY(build_lists(b, s));
+    CMG_TRY(allow_max_dynamic_smem((const void *)k_order_level));
+    b->ev_fork.assign(L, nullptr);
+    b->ev_join.assign(L, nullptr);
+    for (int j = 0; j < L; j++) {
+        CMG_CUDA(cudaEventCreateWithFlags(&b->ev_fork[j], cudaEventDisableTiming));
+        CMG_CUDA(cudaEventCreateWithFlags(&b->ev_join[j], cudaEventDisableTiming));
+    }
     for (int j = 0; j < L; j++) {
         b->lv[j].shape = default_shape(b->lv[j]);
         CMG_TRY(level_workspace(b, j, s));
@@ -1146,7 +1264,8 @@ extern "C" cmg_status_t cmg_setup_batch(int32_t num_graphs, const int64_t *graph
     b->G = num_graphs;
     b->stream = (cudaStream_t)stream;
     if (cudaGetDevice(&b->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking) != cudaSuccess) {
         free_batch(b);
         return CMG_ERR_CUDA;
     }
@@ -1171,10 +1290,12 @@ extern "C" cmg_status_t cmg_fiedler_batch(cmg_batch_t b, double *u_out, int32_t 
         // eager launches with an event pair around each level
         std::vector<cudaEvent_t> ev(2 * L);
         for (auto &e : ev) CMG_CUDA(cudaEventCreate(&e));
-        cmg_status_t st = from_cuda(cudaMemsetAsync(b->queue, 0, sizeof(int) * L, s));
+        cmg_status_t st = from_cuda(cudaMemsetAsync(b->queue, 0, sizeof(int) * 2 * L, s));
         for (int j = L - 1; j >= 0 && st == CMG_OK; j--) {
+            bool ordered = false;
             cudaEventRecord(ev[2 * j], s);
-            st = launch_level(b, j, -1, s);
+            st = order_level(b, j, s, &ordered);
+            if (st == CMG_OK) st = launch_level(b, j, -1, s, ordered);
             cudaEventRecord(ev[2 * j + 1], s);
         }
         if (st == CMG_OK) st = from_cuda(cudaStreamSynchronize(s));
@@ -1335,22 +1456,44 @@ extern "C" cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t s
     return CMG_OK;
 }
 
+// Autotuning replays every graph's real sweep counts, scaled down by
+// kTuneScale, so a candidate shape is timed on the level's real mix of long
+// and short sweep chains (the slowest graphs decide a level's time).
+constexpr int kTuneScale = 8;
+
 extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
     if (!b) return CMG_ERR_INVALID_ARG;
     DeviceGuard dg(b->device);
     cudaStream_t s = (cudaStream_t)stream;
+    const int L = (int)b->lv.size(), G = b->G;
+    // 1. one solve with the current shapes gives the sweep counts
+    CMG_CUDA(cudaMemsetAsync(b->queue, 0, sizeof(int) * 2 * L, s));
+    for (int j = L - 1; j >= 0; j--) {
+        bool ordered = false;
+        CMG_TRY(order_level(b, j, s, &ordered));
+        CMG_TRY(launch_level(b, j, -1, s, ordered));
+    }
+    std::vector<int> sw((size_t)L * G);
+    CMG_CUDA(cudaMemcpyAsync(sw.data(), b->sweeps, sizeof(int) * sw.size(), cudaMemcpyDeviceToHost, s));
+    CMG_CUDA(cudaStreamSynchronize(s));
+    std::vector<int> rep((size_t)G * CMG_MAX_LEVELS, 1);
+    for (int q = 0; q < G; q++)
+        for (int j = 0; j <= b->J[q] && j < CMG_MAX_LEVELS; j++)
+            rep[(size_t)q * CMG_MAX_LEVELS + j] = std::max(1, (sw[(size_t)j * G + q] + kTuneScale - 1) / kTuneScale);
+    CMG_TRY(dev_alloc_n(&b->tune_replay, rep.size(), s));
+    CMG_CUDA(cudaMemcpyAsync(b->tune_replay, rep.data(), sizeof(int) * rep.size(), cudaMemcpyHostToDevice, s));
     cudaEvent_t e0, e1;
     CMG_CUDA(cudaEventCreate(&e0));
     CMG_CUDA(cudaEventCreate(&e1));
     cmg_status_t st = CMG_OK;
-    const int L = (int)b->lv.size();
-    // time one level with a shape: Gaussian starts, 4 sweeps per graph
+    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+    // 2. per level, coarse to fine (a level's order uses the replayed counts
+    // of the level below it), time the candidate shapes
     auto time_shape = [&](int j, const cmg_batch_shape_t &sh, float *ms) -> cmg_status_t {
         BLevel &V = b->lv[j];
         V.shape = sh;
         CMG_TRY(level_workspace(b, j, s));
         int per_sm = 0;
-        const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
         CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, (const void *)batch_kernel(fp32, V.lay.col16, sh.lanes_per_row), threads_for_gpc(sh),
             (size_t)V.smem_group * sh.graphs_per_cta));
@@ -1358,21 +1501,17 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
             *ms = 1e30f;
             return CMG_OK;
         }
-        float best = 1e30f;
-        for (int rep = 0; rep < 3; rep++) {
-            CMG_CUDA(cudaMemsetAsync(b->queue + j, 0, sizeof(int), s));
-            CMG_CUDA(cudaEventRecord(e0, s));
-            CMG_TRY(launch_level(b, j, 4, s));
-            CMG_CUDA(cudaEventRecord(e1, s));
-            CMG_CUDA(cudaEventSynchronize(e1));
-            float t = 0.f;
-            CMG_CUDA(cudaEventElapsedTime(&t, e0, e1));
-            if (rep > 0) best = std::min(best, t);
-        }
-        *ms = best;
+        CMG_CUDA(cudaMemsetAsync(b->queue + 2 * j, 0, 2 * sizeof(int), s));
+        CMG_CUDA(cudaEventRecord(e0, s));
+        bool ordered = false;
+        CMG_TRY(order_level(b, j, s, &ordered));
+        CMG_TRY(launch_level(b, j, -1, s, ordered));
+        CMG_CUDA(cudaEventRecord(e1, s));
+        CMG_CUDA(cudaEventSynchronize(e1));
+        CMG_CUDA(cudaEventElapsedTime(ms, e0, e1));
         return CMG_OK;
     };
-    for (int j = 0; j < L && st == CMG_OK; j++) {
+    for (int j = L - 1; j >= 0 && st == CMG_OK; j--) {
         if (b->lv[j].count == 0) continue;
         cmg_batch_shape_t best = b->lv[j].shape;
         float best_ms = 1e30f;
@@ -1386,15 +1525,14 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
             }
             return CMG_OK;
         };
-        // threads per graph x graphs per CTA, then lanes per row, then staging
+        // threads per graph x graphs per CTA, then lanes per heavy row, then staging
         const int lanes0 = best.lanes_per_row;
         for (int tpg : {32, 64, 128, 256, 512})
-            for (int cta : {128, 256, 512}) {
-                cmg_batch_shape_t sh = {tpg, lanes0, std::max(1, cta / tpg), 1};
-                if (tpg > cta) continue;
-                if ((st = consider(sh)) != CMG_OK) break;
+            for (int cta : {256, 512, 1024}) {
+                if (tpg > cta || st != CMG_OK) continue;
+                st = consider(cmg_batch_shape_t{tpg, lanes0, std::max(1, cta / tpg), 1});
             }
-        for (int lpr : {1, 2, 4, 8, 16}) {
+        for (int lpr : {1, 4, 16, 32}) {
             if (st != CMG_OK) break;
             cmg_batch_shape_t sh = best;
             sh.lanes_per_row = lpr;
@@ -1402,7 +1540,7 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
         }
         if (st == CMG_OK) {
             cmg_batch_shape_t sh = best;
-            sh.stage_csr = 0;
+            sh.stage_csr = 1 - sh.stage_csr;
             st = consider(sh);
         }
         b->lv[j].shape = best;
@@ -1410,6 +1548,9 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaStreamSynchronize(s);
+    dev_free(b->tune_replay, s);
+    b->tune_replay = nullptr;
     drop_graph(b);
     return st;
 }

@@ -128,4 +128,39 @@ __device__ __forceinline__ int start_exponent(double ss0) {
 // x * 2^e for a normal float x and a small e (exponent arithmetic, exact).
 __device__ __forceinline__ float scale2f(float x, int e) { return __int_as_float(__float_as_int(x) + (e << 23)); }
 
+// Sum over the entries f = f0, f0 + stride, ... < f1 of a row: FP32 edge form
+// sum w (x_i - x_j), FP64 degree form sum w x_j.  Entries are taken in
+// groups of 8 -- all column loads, then all gathers -- so a long row costs
+// one round trip to memory per 8 entries, not per entry.  `ld` loads x.
+template <typename T, typename IDX, typename LD>
+__device__ __forceinline__ T row_sum_grouped(const IDX *C, const T *W, int f0, int f1, int stride, T xi,
+                                             LD ld) {
+    T a0 = (T)0, a1 = (T)0;
+    for (int f = f0; f < f1; f += 8 * stride) {
+        int cc[8];
+        T ww[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            const int g = f + u * stride;
+            const bool ok = g < f1;
+            cc[u] = ok ? (int)C[g] : -1;
+            ww[u] = ok ? W[g] : (T)0;
+        }
+        T xx[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) xx[u] = (cc[u] >= 0) ? ld(cc[u]) : xi;
+#pragma unroll
+        for (int u = 0; u < 8; u++) {
+            if (sizeof(T) == 8) {
+                if (u & 1) a1 = fma(ww[u], xx[u], a1);
+                else a0 = fma(ww[u], xx[u], a0);
+            } else {
+                if (u & 1) a1 += ww[u] * (xi - xx[u]);
+                else a0 += ww[u] * (xi - xx[u]);
+            }
+        }
+    }
+    return a0 + a1;
+}
+
 }  // namespace cmg

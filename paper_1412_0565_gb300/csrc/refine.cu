@@ -557,9 +557,23 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSy
     const int *__restrict__ SO = M + h;
     const IDX *__restrict__ C = reinterpret_cast<const IDX *>(a.lay_col);
     const T *__restrict__ W = reinterpret_cast<const T *>(a.lay_w);
-    // work of this CTA: a contiguous range of slices; heavy rows go round robin
-    const int sb = (int)((long long)nsl * blockIdx.x / gridDim.x);
-    const int se = (int)((long long)nsl * (blockIdx.x + 1) / gridDim.x);
+    // work of this CTA: a contiguous range of slices holding about 1/gridDim
+    // of the slice entries (the slices are sorted by width, so equal slice
+    // counts would not balance); heavy rows go round robin over all warps
+    __shared__ int s_range[2];
+    if (threadIdx.x < 2) {
+        const long long tot = (long long)SO[nsl] - SO[0];
+        const long long target = SO[0] + tot * (blockIdx.x + threadIdx.x) / gridDim.x;
+        int lo = 0, hi = nsl;   // first slice starting at or after the target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (SO[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        s_range[threadIdx.x] = (blockIdx.x + threadIdx.x == gridDim.x) ? nsl : lo;
+    }
+    __syncthreads();
+    const int sb = s_range[0], se = s_range[1];
     const int r0 = (int)((long long)n * blockIdx.x / gridDim.x);
     const int r1 = (int)((long long)n * (blockIdx.x + 1) / gridDim.x);
 
@@ -675,46 +689,19 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSy
             // heavy rows: a warp per row
             for (int r = gw; r < h; r += ngw) {
                 const T xi = LDXG(x + r);
-                T ac = (T)0;
-                for (int f = M[r] + lane, f1 = M[r + 1]; f < f1; f += 32) {
-                    const T xj = LDXG(x + C[f]);
-                    if (fp64) ac = fma(W[f], xj, ac);
-                    else ac += W[f] * (xi - xj);
-                }
+                T ac = row_sum_grouped<T, IDX>(C, W, M[r] + lane, M[r + 1], 32, xi,
+                                               [&](int c) { return LDXG(x + c); });
                 ac = warp_sum(ac);
                 if (lane == 0) finish(r, xi, ac);
             }
-            // slices: a lane per row
+            // slices: a lane per row, entries in groups of 8 (row_sum_grouped)
             for (int q = sb + rw; q < se; q += nrw) {
                 const int i = h + 32 * q + lane;
                 const int so = SO[q] + lane, wd = (SO[q + 1] - SO[q]) >> 5;
                 const T xi = (i < n) ? LDXG(x + i) : (T)0;
-                T a0 = (T)0, a1 = (T)0, a2 = (T)0, a3 = (T)0;
-                int k = 0;
-                for (; k + 3 < wd; k += 4) {
-                    const int f = so + 32 * k;
-                    const int c0 = C[f], c1 = C[f + 32], c2 = C[f + 64], c3 = C[f + 96];
-                    const T w0 = W[f], w1 = W[f + 32], w2 = W[f + 64], w3 = W[f + 96];
-                    const T x0 = LDXG(x + c0), x1 = LDXG(x + c1), x2 = LDXG(x + c2), x3 = LDXG(x + c3);
-                    if (fp64) {
-                        a0 = fma(w0, x0, a0);
-                        a1 = fma(w1, x1, a1);
-                        a2 = fma(w2, x2, a2);
-                        a3 = fma(w3, x3, a3);
-                    } else {
-                        a0 += w0 * (xi - x0);
-                        a1 += w1 * (xi - x1);
-                        a2 += w2 * (xi - x2);
-                        a3 += w3 * (xi - x3);
-                    }
-                }
-                for (; k < wd; k++) {
-                    const int f = so + 32 * k;
-                    const T xv = LDXG(x + C[f]);
-                    if (fp64) a0 = fma(W[f], xv, a0);
-                    else a0 += W[f] * (xi - xv);
-                }
-                if (i < n) finish(i, xi, (a0 + a1) + (a2 + a3));
+                const T ac = row_sum_grouped<T, IDX>(C, W, so, so + 32 * wd, 32, xi,
+                                                     [&](int c) { return LDXG(x + c); });
+                if (i < n) finish(i, xi, ac);
             }
             Part p = warp_sum_part(acc.get());
             if (lane == 0) s_pw[warp] = p;

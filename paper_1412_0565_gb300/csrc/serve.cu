@@ -8,10 +8,13 @@
 //   warm     the graph's hierarchy is resident: cmg_fiedler only;
 //   single   a large graph (n > batch_max_n) without a hierarchy: cmg_setup,
 //            cmg_fiedler, and the hierarchy stays resident (keep_resident);
-//   batch    small graphs without a hierarchy: every such pending request
-//            (up to max_batch) joins one cmg_setup_batch / cmg_fiedler_batch,
-//            so requests that arrive while others run are admitted together
-//            as soon as a worker and memory free up (continuous batching).
+//   batch    small graphs without a hierarchy, when at least min_batch of
+//            them are pending: every such request (up to max_batch) joins one
+//            cmg_setup_batch / cmg_fiedler_batch, so requests that arrive
+//            while others run are admitted together as soon as a worker and
+//            memory free up (continuous batching).  With fewer pending, a
+//            small graph runs alone like a large one: a batched job gives a
+//            graph one group of threads, the single form the whole GPU.
 // A request's result does not depend on the job it ran in beyond rounding:
 // the batched form computes each graph's hierarchy bit for bit as the single
 // form does.
@@ -128,7 +131,16 @@ Job pick_job(cmg_server_s *S) {
             return job;
         }
         const size_t est = estimate(S, g);
-        const bool small = g.n <= S->cfg.batch_max_n && S->cfg.max_batch > 1;
+        bool small = g.n <= S->cfg.batch_max_n && S->cfg.max_batch > 1;
+        if (small) {
+            // batch only when enough small cold requests wait for it
+            int waiting = 0;
+            for (auto jt = it; jt != S->pending.end() && waiting < S->cfg.min_batch; ++jt) {
+                const Graph &gj = S->graphs[(*jt)->gid];
+                if (!gj.busy && !gj.h && gj.n <= S->cfg.batch_max_n) waiting++;
+            }
+            small = waiting >= S->cfg.min_batch;
+        }
         if (!small) {
             if (!make_room(S, est)) {
                 if (S->running == 0 && S->used == 0) {
@@ -327,6 +339,7 @@ extern "C" cmg_status_t cmg_server_config_default(cmg_server_config_t *cfg) {
     cfg->batch_max_n = 50000;
     cfg->mem_budget = 0;
     cfg->keep_resident = 1;
+    cfg->min_batch = 32;
     return CMG_OK;
 }
 
@@ -337,8 +350,9 @@ extern "C" cmg_status_t cmg_server_create(const cmg_server_config_t *cfg, const 
     cmg_server_config_t c;
     cmg_server_config_default(&c);
     if (cfg) c = *cfg;
-    if (c.workers < 1 || c.workers > 64 || c.max_batch < 1 || c.batch_max_n < 0 || c.reserved != 0)
+    if (c.workers < 1 || c.workers > 64 || c.max_batch < 1 || c.batch_max_n < 0 || c.min_batch < 0)
         return CMG_ERR_INVALID_ARG;
+    if (c.min_batch == 0) c.min_batch = 32;
     cmg_options_t o;
     cmg_options_default(&o);
     if (opts) o = *opts;

@@ -107,8 +107,8 @@ def test_server_argument_errors_need_no_gpu():
     s = C.c_void_p()
     cfg = cmg.ServerConfig()
     assert lib.cmg_server_config_default(C.byref(cfg)) == 0
-    assert cfg.workers == 4 and cfg.max_batch == 256 and cfg.keep_resident == 1
-    for field, bad in (("workers", 0), ("workers", 65), ("max_batch", 0), ("reserved", 1)):
+    assert cfg.workers == 4 and cfg.max_batch == 256 and cfg.keep_resident == 1 and cfg.min_batch == 32
+    for field, bad in (("workers", 0), ("workers", 65), ("max_batch", 0), ("min_batch", -1)):
         c2 = cmg.ServerConfig.from_buffer_copy(cfg)
         setattr(c2, field, bad)
         assert cmg.STATUS[lib.cmg_server_create(C.byref(c2), None, C.byref(s))] == "ERR_INVALID_ARG"

@@ -110,6 +110,7 @@ SHAPES = [
     (128, 8, 1, 1),
     (256, 16, 2, 1),
     (512, 32, 1, 0),
+    (1024, 4, 1, 1),
 ]
 
 
@@ -152,7 +153,7 @@ def test_batch_autotune_keeps_results(batch_case):
         b.autotune()
         for lvl in range(b.union_levels):
             tpg, lpr, gpc, stage = b.shape(lvl)
-            assert 32 <= tpg <= 512 and lpr in (1, 2, 4, 8, 16, 32) and tpg * gpc <= 512
+            assert 32 <= tpg <= 1024 and lpr in (1, 2, 4, 8, 16, 32) and tpg * gpc <= 1024
         u, lam, res, _ = b.fiedler()
         check_fp64(b, graphs, refs, u, lam, res)
 
@@ -227,3 +228,34 @@ def test_batch_input_errors():
     with pytest.raises(cmg.CmgError) as e:
         cmg.Batch(np.array([0, 12, 10, 22]), rp, col, w)
     assert e.value.name == "ERR_INVALID_ARG"
+
+
+def test_batch_split_levels_match_oracle():
+    """Levels with at least 16 graphs run their largest-work graphs (ordered on
+    the device by the coarser level's sweeps) in a launch of 1024-thread
+    groups beside the rest; every graph still matches the oracle (FP64) and
+    the FP32 gates (replay)."""
+    rng = np.random.default_rng(77)
+    graphs = []
+    for i in range(40):
+        n = int(rng.integers(300, 2500))
+        fam = i % 3
+        if fam == 0:
+            graphs.append(inputs.rgg(n, 8.0, seed=100 + i))
+        elif fam == 1:
+            a = int(np.sqrt(n))
+            graphs.append(inputs.grid2d(a, n // a, "uniform", seed=100 + i))
+        else:
+            graphs.append(inputs.barabasi_albert(n, 4, seed=100 + i))
+    rp, col, w, offs = inputs.concat_csr(graphs)
+    refs = [oracle.fiedler(g[0], g[1], g[2], seed=SEED) for g in graphs]
+    with cmg.Batch(offs, rp, col, w, seed=SEED) as b:
+        u, lam, res, sts = b.fiedler()
+        check_fp64(b, graphs, refs, u, lam, res)
+    with cmg.Batch(offs, rp, col, w, seed=SEED, precision="fp32", schedule="replay") as b:
+        b.set_replay([r[4]["sweeps"].tolist() for r in refs])
+        u, lam, res, _ = b.fiedler()
+        for q, ref in enumerate(refs):
+            uq = u[offs[q]:offs[q + 1]]
+            assert abs(lam[q] - ref[1]) <= 1e-6 * abs(ref[1]), q
+            assert angle(uq, ref[0]) <= 1e-4, q

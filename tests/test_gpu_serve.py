@@ -58,7 +58,7 @@ def run_all(server, gids, concurrent):
 
 def test_same_result_alone_and_in_the_mix():
     gs = graphs()
-    with cmg.Server(workers=3, max_batch=64, batch_max_n=5000, seed=1412) as mix:
+    with cmg.Server(workers=3, max_batch=64, batch_max_n=5000, min_batch=2, seed=1412) as mix:
         ids = [mix.add_graph(*g) for g in gs]
         res_mix = run_all(mix, ids, concurrent=True)
         st = mix.stats()
@@ -108,7 +108,8 @@ def test_admission_under_a_small_memory_budget():
     gs = graphs()
     est = [cmg.estimate_device_bytes(len(g[0]) - 1, int(g[0][-1])) for g in gs]
     budget = max(est) + 1
-    with cmg.Server(workers=4, max_batch=64, batch_max_n=5000, mem_budget=budget, seed=1412) as srv:
+    with cmg.Server(workers=4, max_batch=64, batch_max_n=5000, min_batch=2, mem_budget=budget,
+                    seed=1412) as srv:
         ids = [srv.add_graph(*g) for g in gs]
         res = run_all(srv, ids, concurrent=True)
         st = srv.stats()
@@ -141,7 +142,7 @@ def test_repeated_graphs_under_poisson_arrivals_all_complete():
         ids = [srv.add_graph(*g) for g in gs]
         for k in sorted(set(trace.tolist())):
             alone[k] = srv.wait(srv.submit(ids[k]), timeout_s=120)
-    with cmg.Server(workers=4, max_batch=64, batch_max_n=5000, seed=1412) as srv:
+    with cmg.Server(workers=4, max_batch=64, batch_max_n=5000, min_batch=2, seed=1412) as srv:
         ids = [srv.add_graph(*g) for g in gs]
         arr = np.cumsum(rng.exponential(0.004, size=len(trace)))
         t0 = time.perf_counter()
