@@ -332,6 +332,9 @@ def run_gpu(args):
     serving = None
     if not args.no_serving and world == 1:
         serving = run_serving(args)
+    chung_lu = None
+    if not args.no_chung_lu and world == 1:
+        chung_lu = run_chung_lu(args, stream, flush)
 
     if rank == 0:
         cpu = None
@@ -376,6 +379,7 @@ def run_gpu(args):
             "clocks": clocks,
             "batch": batch,
             "serving": serving,
+            "chung_lu": chung_lu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -507,6 +511,67 @@ def run_batch(args, stream, flush):
     return res
 
 
+CL_WORKLOAD = ("Chung-Lu power-law graph, n 4,194,304 before the largest component, mean degree 16, "
+               "exponent 2.5, degrees capped at sqrt(16 n), lognormal(0,1) weights, seed 1412")
+
+
+def run_chung_lu(args, stream, flush):
+    """Config 3: one large power-law graph through the single-graph path, FP32
+    sweeps against the FP64 form (setup + solve per step)."""
+    import torch
+    from paper_1412_0565_gb300 import cmg, inputs
+    t0 = time.perf_counter()
+    rp, col, w = inputs.chung_lu(4_194_304, seed=1412)
+    gen_s = time.perf_counter() - t0
+    n, nnz = len(rp) - 1, int(rp[-1])
+    sid = stream.cuda_stream
+    drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    deg = rp[1:] - rp[:-1]
+    out = {"workload": CL_WORKLOAD, "n": n, "nnz": nnz, "max_degree": int(deg.max()),
+           "generate_s": round(gen_s, 1)}
+    res = {}
+    for prec in ("fp32", "fp64"):
+        opts = cmg.options(seed=1412, precision=prec, timing=1)
+        ms, setup = [], []
+        for k in range(args.cl_warmup + args.cl_steps):
+            flush.zero_()
+            e0, em, e1 = (torch.cuda.Event(enable_timing=True) for _e in range(3))
+            e0.record(stream)
+            h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
+            em.record(stream)
+            _u, lam, st = h.fiedler(u_out=u, stream=sid)
+            e1.record(stream)
+            e1.synchronize()
+            h.close()
+            if k >= args.cl_warmup:
+                ms.append(e0.elapsed_time(e1))
+                setup.append(e0.elapsed_time(em))
+        by0 = st["sweeps"][0] * ((8 if prec == "fp32" else 12) * st["nnz"][0] + (12 if prec == "fp32" else 20) * st["n"][0])
+        res[prec] = {"u": u.cpu().numpy(), "lam": lam, "sweeps": st["sweeps"]}
+        out[prec] = {"value": len(ms) / (sum(ms) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ms),
+                     "setup_ms": statistics.mean(setup), "levels": st["levels"], "sweeps": st["sweeps"],
+                     "level_n": st["n"], "level_nnz": st["nnz"],
+                     "level_ms": [round(x, 3) for x in st["level_ms"]], "lambda2": lam,
+                     "residual": st["residual"],
+                     "level0_launch": {"ms": st["level_ms"][0], "algorithmic_bytes": by0,
+                                       "achieved_gbs": by0 / (st["level_ms"][0] * 1e-3) / 1e9}}
+    # precision alone: FP32 sweeps replaying the FP64 sweep counts
+    h = cmg.Hierarchy(drp, dcol, dw, seed=1412, precision="fp32", schedule="replay",
+                      replay_sweeps=res["fp64"]["sweeps"], stream=sid)
+    _u, lam32, _ = h.fiedler(u_out=u, stream=sid)
+    h.close()
+    u32, u64 = u.cpu().numpy(), res["fp64"]["u"]
+    c = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
+    out["fp32_vs_fp64_replay"] = {"lambda2_rel": abs(lam32 - res["fp64"]["lam"]) / abs(res["fp64"]["lam"]),
+                                  "angle": float(np.arccos(min(1.0, c)))}
+    c2 = abs(float(np.dot(res["fp32"]["u"], u64))) / (np.linalg.norm(res["fp32"]["u"]) * np.linalg.norm(u64))
+    out["fp32_vs_fp64_tolerance_mode"] = {
+        "lambda2_rel": abs(res["fp32"]["lam"] - res["fp64"]["lam"]) / abs(res["fp64"]["lam"]),
+        "angle": float(np.arccos(min(1.0, c2)))}
+    return out
+
+
 def run_serving(args):
     """Request loop: closed-loop saturation, then Poisson arrivals at 0.8 of
     it; FP32 server (batching, resident hierarchies) and plain FP64 server
@@ -586,6 +651,9 @@ def main():
     ap.add_argument("--serve-graphs", type=int, default=48)
     ap.add_argument("--serve-requests", type=int, default=160)
     ap.add_argument("--serve-replay-sample", type=int, default=16)
+    ap.add_argument("--no-chung-lu", action="store_true")
+    ap.add_argument("--cl-steps", type=int, default=3)
+    ap.add_argument("--cl-warmup", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

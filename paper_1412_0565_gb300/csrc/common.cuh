@@ -75,6 +75,7 @@ struct DeviceInfo {
     int device;
     int sms;
     int max_smem_optin;
+    int l2_bytes;
 };
 cmg_status_t device_info(DeviceInfo *out);
 

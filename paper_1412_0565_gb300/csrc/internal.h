@@ -60,7 +60,10 @@ cmg_status_t launch_to_float(long long m, const double *w, float *w32, cudaStrea
 // Columns are renumbered local ids (16-bit when every graph of the level
 // has at most 65536 vertices).  meta of a graph: the entry offsets (local to
 // the graph) of its h heavy rows, then of its nsl slices, then the end.
-constexpr int kHeavy = 32;
+#ifndef CMG_HEAVY_ROW
+#define CMG_HEAVY_ROW 128
+#endif
+constexpr int kHeavy = CMG_HEAVY_ROW;
 
 struct SweepLayout {
     uint32_t *perm = nullptr;   // new position -> original vertex (union numbering)
@@ -74,7 +77,14 @@ struct SweepLayout {
     int col16 = 1;
     long long entries = 0;
     std::vector<int> hecnt, hmcnt, hheavy;   // per graph, host copies
+    // single-graph layouts: heavy rows cut into chunks of kHeavyChunk entries
+    int *hchunk = nullptr;      // [h+1] first chunk of each heavy row
+    int *crow = nullptr;        // [nchunks] heavy row of each chunk
+    int *hcount = nullptr;      // [h] chunks finished (zeroed per launch)
+    void *cpart = nullptr;      // [nchunks] chunk partial sums (sweep precision)
+    int nchunks = 0;
 };
+constexpr int kHeavyChunk = 2048;
 // Builds the layout of the N rows of a level holding G graphs at union
 // offsets voff (device, G+1; host copy hvoff) from the level's CSR; fp32
 // selects float weights.  Adds its device bytes to *bytes (nullable).

@@ -164,6 +164,18 @@ __global__ void k_layout_fill(int n, int G, const int *__restrict__ voff, const 
 }
 
 
+// chunk counts of the heavy rows of a one-graph layout
+__global__ void k_layout_chunks(int h, const int *__restrict__ meta, int *__restrict__ cnt) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < h; r += gridDim.x * blockDim.x)
+        cnt[r] = (meta[r + 1] - meta[r] + kHeavyChunk - 1) / kHeavyChunk;
+}
+
+// heavy row of every chunk
+__global__ void k_layout_chunk_rows(int h, const int *__restrict__ hchunk, int *__restrict__ crow) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < h; r += gridDim.x * blockDim.x)
+        for (int c = hchunk[r]; c < hchunk[r + 1]; c++) crow[c] = r;
+}
+
 cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &hvoff, int N,
                                 const int *rp, const int *col, const double *w, int fp32,
                                 SweepLayout *L, size_t *bytes, cudaStream_t s) {
@@ -245,11 +257,33 @@ cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &
     else CMG_FILL(double, int);
 #undef CMG_FILL
     CMG_TRY(launch_status());
+    if (G == 1 && L->hheavy[0] > 0) {
+        // heavy rows of a single graph are summed by several warps, a chunk each
+        const int h = L->hheavy[0];
+        int *cnt;
+        CMG_TRY(scr.get(&cnt, (size_t)h));
+        CMG_TRY(dev_alloc_n(&L->hchunk, (size_t)h + 1, s));
+        CMG_TRY(dev_alloc_n(&L->hcount, (size_t)h, s));
+        k_layout_chunks<<<grid_for(h, 256), 256, 0, s>>>(h, L->meta, cnt);
+        CMG_TRY(launch_status());
+        CMG_TRY(exclusive_scan(cnt, L->hchunk, h, scr, s));
+        CMG_CUDA(cudaMemcpyAsync(&L->nchunks, L->hchunk + h, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CMG_CUDA(cudaStreamSynchronize(s));
+        CMG_TRY(dev_alloc(&L->cpart, esz * (size_t)std::max(L->nchunks, 1), s));
+        CMG_TRY(dev_alloc_n(&L->crow, (size_t)std::max(L->nchunks, 1), s));
+        k_layout_chunk_rows<<<grid_for(h, 256), 256, 0, s>>>(h, L->hchunk, L->crow);
+        CMG_TRY(launch_status());
+        if (bytes) *bytes += (size_t)h * 8 + (esz + 4) * (size_t)L->nchunks;
+    }
     if (bytes) *bytes += (size_t)N * 8 + (size_t)G * 12 + (size_t)tm * 4 + (size_t)te * (isz + esz);
     return CMG_OK;
 }
 
 void free_sweep_layout(SweepLayout &L, cudaStream_t s) {
+    dev_free(L.hchunk, s);
+    dev_free(L.crow, s);
+    dev_free(L.hcount, s);
+    dev_free(L.cpart, s);
     dev_free(L.perm, s);
     dev_free(L.inv, s);
     dev_free(L.heavy, s);

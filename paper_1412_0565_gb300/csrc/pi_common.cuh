@@ -134,7 +134,7 @@ __device__ __forceinline__ float scale2f(float x, int e) { return __int_as_float
 // one round trip to memory per 8 entries, not per entry.  `ld` loads x.
 template <typename T, typename IDX, typename LD>
 __device__ __forceinline__ T row_sum_grouped(const IDX *C, const T *W, int f0, int f1, int stride, T xi,
-                                             LD ld) {
+                                             LD ld, bool stream = false) {
     T a0 = (T)0, a1 = (T)0;
     for (int f = f0; f < f1; f += 8 * stride) {
         int cc[8];
@@ -143,8 +143,15 @@ __device__ __forceinline__ T row_sum_grouped(const IDX *C, const T *W, int f0, i
         for (int u = 0; u < 8; u++) {
             const int g = f + u * stride;
             const bool ok = g < f1;
-            cc[u] = ok ? (int)C[g] : -1;
-            ww[u] = ok ? W[g] : (T)0;
+            if (stream) {
+                // global streams read once per sweep: evict-first, so the
+                // gathered iterate keeps its place in L2
+                cc[u] = ok ? (int)__ldcs(C + g) : -1;
+                ww[u] = ok ? __ldcs(W + g) : (T)0;
+            } else {
+                cc[u] = ok ? (int)C[g] : -1;
+                ww[u] = ok ? W[g] : (T)0;
+            }
         }
         T xx[8];
 #pragma unroll

@@ -102,6 +102,12 @@ struct PiArgs {
     const int *lay_meta;
     const void *lay_col;
     const void *lay_w;
+    const int *hchunk;      // heavy rows: first chunk per row ([h+1]), or nullptr
+    const int *crow;        // heavy row of each chunk
+    int *hcount;            // chunks finished per heavy row
+    void *cpart;            // chunk partial sums
+    int nchunks;
+    int stream_hint;        // the layout is larger than L2: read it evict-first
 };
 
 
@@ -541,7 +547,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
 // per row; entry k of the slice's rows is one coalesced load), so the loads of
 // a sweep do not wait on one another and no CTA barrier is needed inside a
 // sweep.  The iterates are stored in layout order.
-template <typename T, typename IDX>
+template <typename T, typename IDX, bool CHUNKS, bool STREAM>
 __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSync *gs) {
     __shared__ Part s_pw[kTileThreads / 32];
     __shared__ Slot s_slot[2];
@@ -686,21 +692,38 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSy
                 y[i] = yv;
                 acc.add(yv, xi);
             };
-            // heavy rows: a warp per row
-            for (int r = gw; r < h; r += ngw) {
+            auto ldx = [&](int c) { return LDXG(x + c); };
+            // heavy rows: cut into chunks of kHeavyChunk entries, a warp per
+            // chunk; the warp that finishes a row's last chunk sums the row's
+            // chunk partials in chunk order and completes the row
+            for (int cidx = gw; CHUNKS && cidx < a.nchunks; cidx += ngw) {
+                const int r = a.crow[cidx], c0 = a.hchunk[r], nc = a.hchunk[r + 1] - c0;
+                const int f0 = M[r] + (cidx - c0) * kHeavyChunk;
+                const int f1 = min(M[r + 1], f0 + kHeavyChunk);
                 const T xi = LDXG(x + r);
-                T ac = row_sum_grouped<T, IDX>(C, W, M[r] + lane, M[r + 1], 32, xi,
-                                               [&](int c) { return LDXG(x + c); });
+                T ac = row_sum_grouped<T, IDX>(C, W, f0 + lane, f1, 32, xi, ldx, STREAM);
                 ac = warp_sum(ac);
-                if (lane == 0) finish(r, xi, ac);
+                if (nc == 1) {
+                    if (lane == 0) finish(r, xi, ac);
+                } else if (lane == 0) {
+                    T *cp = reinterpret_cast<T *>(a.cpart);
+                    cp[cidx] = ac;
+                    __threadfence();
+                    const int done = atomicAdd(a.hcount + r, 1);
+                    if (done == (s + 1) * nc - 1) {
+                        __threadfence();
+                        T tot = (T)0;
+                        for (int c = c0; c < c0 + nc; c++) tot += __ldcg(cp + c);
+                        finish(r, xi, tot);
+                    }
+                }
             }
             // slices: a lane per row, entries in groups of 8 (row_sum_grouped)
             for (int q = sb + rw; q < se; q += nrw) {
                 const int i = h + 32 * q + lane;
                 const int so = SO[q] + lane, wd = (SO[q + 1] - SO[q]) >> 5;
                 const T xi = (i < n) ? LDXG(x + i) : (T)0;
-                const T ac = row_sum_grouped<T, IDX>(C, W, so, so + 32 * wd, 32, xi,
-                                                     [&](int c) { return LDXG(x + c); });
+                const T ac = row_sum_grouped<T, IDX>(C, W, so, so + 32 * wd, 32, xi, ldx, STREAM);
                 if (i < n) finish(i, xi, ac);
             }
             Part p = warp_sum_part(acc.get());
@@ -1027,6 +1050,17 @@ static size_t tiled_smem(bool fp32) {
     return ts + e * 2 * kTileRows + sizeof(int) * (kTileRows + 4) + 2 * kChunk;
 }
 
+template <typename T, typename IDX>
+static const void *sell_kernel_ti(bool chunks, bool stream) {
+    if (chunks) return stream ? (const void *)k_power_sell<T, IDX, true, true> : (const void *)k_power_sell<T, IDX, true, false>;
+    return stream ? (const void *)k_power_sell<T, IDX, false, true> : (const void *)k_power_sell<T, IDX, false, false>;
+}
+
+static const void *sell_kernel(int fp32, int col16, bool chunks, bool stream) {
+    if (fp32) return col16 ? sell_kernel_ti<float, uint16_t>(chunks, stream) : sell_kernel_ti<float, int>(chunks, stream);
+    return col16 ? sell_kernel_ti<double, uint16_t>(chunks, stream) : sell_kernel_ti<double, int>(chunks, stream);
+}
+
 template <typename T>
 static const void *small_kernel(int G) {
     switch (G) {
@@ -1148,6 +1182,12 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.lay_h = a.lay_nsl = 0;
     a.lay_meta = nullptr;
     a.lay_col = a.lay_w = nullptr;
+    a.hchunk = nullptr;
+    a.crow = nullptr;
+    a.hcount = nullptr;
+    a.cpart = nullptr;
+    a.nchunks = 0;
+    a.stream_hint = 0;
     void *args[] = {&a, &gs};
     if (small_level_fits(lv, run.fp32)) {
         const int G = small_lanes(lv.n, lv.nnz, run.fp32);
@@ -1163,16 +1203,32 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
         a.perm = reinterpret_cast<const int *>(L.perm);
         a.lay_h = L.hheavy[0];
         a.lay_nsl = (lv.n - a.lay_h + 31) / 32;
+        {
+            // layout bytes against L2: only a stream that cannot stay in L2
+            // is read evict-first
+            DeviceInfo di;
+            CMG_TRY(device_info(&di));
+            const int l2 = di.l2_bytes;
+            const long long lay_bytes = L.entries * (long long)((L.col16 ? 2 : 4) + (run.fp32 ? 4 : 8));
+            a.stream_hint = (l2 > 0 && lay_bytes > (long long)l2) ? 1 : 0;
+        }
         a.lay_meta = L.meta;
         a.lay_col = L.bcol;
         a.lay_w = L.bw;
-        const void *kern;
-        if (run.fp32) kern = L.col16 ? (const void *)k_power_sell<float, uint16_t> : (const void *)k_power_sell<float, int>;
-        else kern = L.col16 ? (const void *)k_power_sell<double, uint16_t> : (const void *)k_power_sell<double, int>;
+        a.hchunk = L.hchunk;
+        a.crow = L.crow;
+        a.hcount = L.hcount;
+        a.cpart = L.cpart;
+        a.nchunks = L.nchunks;
+        if (a.lay_h > 0) {
+            if (!L.hchunk) return CMG_ERR_INVALID_ARG;
+            CMG_CUDA(cudaMemsetAsync(L.hcount, 0, sizeof(int) * (size_t)a.lay_h, s));
+        }
+        const void *kern = sell_kernel(run.fp32, L.col16, a.lay_h > 0, a.stream_hint != 0);
         int maxb = 0;
         CMG_TRY(coop_max_blocks(kern, kTileThreads, 0, &maxb));
         const int row_warps = kTileThreads / 32 - 1;
-        const long long tasks = (long long)a.lay_nsl + a.lay_h;
+        const long long tasks = (long long)a.lay_nsl + a.nchunks;
         const int blocks = (int)std::max<long long>(1, std::min<long long>(maxb, (tasks + row_warps - 1) / row_warps));
         double *partials;
         if (ws) {

@@ -113,6 +113,7 @@ cmg_status_t device_info(DeviceInfo *out) {
     d.device = dev;
     CMG_CUDA(cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev));
     CMG_CUDA(cudaDeviceGetAttribute(&d.max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    CMG_CUDA(cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev));
     std::lock_guard<std::mutex> lk(g_pool_mutex);
     g_info[dev] = d;
     g_info_ok[dev] = true;
