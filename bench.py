@@ -218,12 +218,15 @@ def run_gpu(args):
         """Timed steps of setup + solve with device-resident inputs."""
         opts = cmg.options(seed=1412, timing=1, precision=precision)
         u = torch.empty(n, dtype=torch.float64, device="cuda")
+        kinds = {}
 
         def step(mid=None):
             h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
             if mid is not None:
                 mid.record(stream)
             _, lam, st = h.fiedler(u_out=u, stream=sid)
+            if not kinds:
+                kinds["k"] = h.level_kernels()
             h.close()
             return lam, st
 
@@ -256,7 +259,8 @@ def run_gpu(args):
                 "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
                 "setup_ms": statistics.median(setup_ms),
                 "solve_ms": statistics.median(a - b for a, b in zip(step_ms, setup_ms)),
-                "stats": stats, "launches": launches, "u": u.cpu().numpy(), "lam": lam}
+                "stats": stats, "launches": launches, "u": u.cpu().numpy(), "lam": lam,
+                "kinds": kinds["k"]}
 
     with ClockSampler(local) as clk:
         r32 = measure("fp32", args.steps, args.warmup)
@@ -361,6 +365,7 @@ def run_gpu(args):
             "latency_ms": {"p50": r32["p50_ms"], "p99": r32["p99_ms"]},
             "split_ms": {"setup": r32["setup_ms"], "solve": r32["solve_ms"]},
             "levels": {"n": st32["n"], "nnz": st32["nnz"], "sweeps": st32["sweeps"],
+                       "kernel": [KERNEL_KIND[k] for k in r32["kinds"][0]],
                        "level_ms": [round(x, 4) for x in st32["level_ms"]]},
             "lambda2": st32["lambda2"], "residual": st32["residual"],
             "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
@@ -543,6 +548,7 @@ def run_chung_lu(args, stream, flush):
             _u, lam, st = h.fiedler(u_out=u, stream=sid)
             e1.record(stream)
             e1.synchronize()
+            kinds = h.level_kernels()
             h.close()
             if k >= args.cl_warmup:
                 ms.append(e0.elapsed_time(e1))
@@ -552,6 +558,7 @@ def run_chung_lu(args, stream, flush):
         out[prec] = {"value": len(ms) / (sum(ms) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ms),
                      "setup_ms": statistics.mean(setup), "levels": st["levels"], "sweeps": st["sweeps"],
                      "level_n": st["n"], "level_nnz": st["nnz"],
+                     "level_kernel": [KERNEL_KIND[k] for k in kinds[0]], "level_staged": kinds[1],
                      "level_ms": [round(x, 3) for x in st["level_ms"]], "lambda2": lam,
                      "residual": st["residual"],
                      "level0_launch": {"ms": st["level_ms"][0], "algorithmic_bytes": by0,
@@ -570,6 +577,9 @@ def run_chung_lu(args, stream, flush):
         "lambda2_rel": abs(res["fp32"]["lam"] - res["fp64"]["lam"]) / abs(res["fp64"]["lam"]),
         "angle": float(np.arccos(min(1.0, c2)))}
     return out
+
+
+KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled"}
 
 
 def run_serving(args):

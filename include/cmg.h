@@ -152,6 +152,17 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
 cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_per_level,
                                 int64_t *nnz_per_level);
 
+/* Sweep kernel that runs Alg. 3 on each level (host arrays of length >= levels,
+ * nullable).  kind_out[j]: 0 = one CTA with the level in shared memory,
+ * 1 = slice kernel over the level's sweep layout, 2 = the same with the
+ * iterate's first staged_out[j] entries (its highest-degree rows) copied to
+ * shared memory every sweep, 3 = row-tile kernel.  Staging is chosen at setup
+ * where the gathers it serves are several per staged entry and SM; the
+ * environment variable CMG_STAGE=0 (never) or CMG_STAGE=1 (every slice
+ * level), read by cmg_setup, overrides that.  Results do not depend on the
+ * kernel.  Errors: INVALID_ARG if h is NULL. */
+cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *staged_out);
+
 /* Device bytes held by the hierarchy (levels and solve workspace). */
 cmg_status_t cmg_hierarchy_device_bytes(cmg_hierarchy_t h, size_t *bytes);
 

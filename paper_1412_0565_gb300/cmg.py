@@ -33,7 +33,7 @@ STATUS = {
 # every symbol include/cmg.h declares
 EXPORTS = [
     "cmg_options_default", "cmg_status_string", "cmg_version", "cmg_setup", "cmg_fiedler",
-    "cmg_hierarchy_info", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
+    "cmg_hierarchy_info", "cmg_level_kernels", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
     "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
     "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
     "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
@@ -142,6 +142,7 @@ def load(build_if_stale: bool = True):
             "cmg_setup": (I32, [I64, V, V, V, I32, P(Options), V, P(V)]),
             "cmg_fiedler": (I32, [V, V, I32, P(F64), P(Stats), V]),
             "cmg_hierarchy_info": (I32, [V, P(I32), V, V]),
+            "cmg_level_kernels": (I32, [V, V, V]),
             "cmg_hierarchy_device_bytes": (I32, [V, P(C.c_size_t)]),
             "cmg_estimate_device_bytes": (I32, [I64, I64, I32, P(C.c_size_t)]),
             "cmg_get_aggregates": (I32, [V, I32, V]),
@@ -308,6 +309,17 @@ class Hierarchy:
         _check(load().cmg_hierarchy_info(self._h, None, C.c_void_p(n.ctypes.data),
                                          C.c_void_p(nnz.ctypes.data)), "info")
         return n.tolist(), nnz.tolist()
+
+    def level_kernels(self):
+        """Per level: (kind, staged) -- kind 0 shared-memory kernel, 1 slice
+        kernel, 2 slice kernel with `staged` iterate entries staged in shared
+        memory, 3 row-tile kernel."""
+        L = self.levels
+        kind = np.zeros(L, dtype=np.int32)
+        staged = np.zeros(L, dtype=np.int32)
+        _check(load().cmg_level_kernels(self._h, C.c_void_p(kind.ctypes.data),
+                                        C.c_void_p(staged.ctypes.data)), "level_kernels")
+        return kind.tolist(), staged.tolist()
 
     def device_bytes(self) -> int:
         b = C.c_size_t()

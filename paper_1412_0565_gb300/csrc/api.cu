@@ -1,6 +1,7 @@
 // api.cu -- the C-ABI of libcmg (include/cmg.h): input validation, the
 // resident hierarchy of Alg. 1 Step 1, and the solve of Alg. 1 Steps 2-3.
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -329,20 +330,30 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     // ---- SELL-32 sizes (small levels); sweep layouts for the levels the
     // shared-memory kernel cannot hold
     size_t lay_bytes = 0;
+    const int nlev = (int)h->lv.size();
+    std::vector<int> stage_try(nlev, 0);
+    std::vector<unsigned long long> below(nlev, 0);
+    unsigned long long *below_dev = nullptr;
     {
         unsigned long long *cnt;
         int *voff1;
         CMG_TRY(scr.get(&cnt, 1));
         CMG_TRY(scr.get(&voff1, 2));
+        CMG_TRY(scr.get(&below_dev, (size_t)nlev));
         const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
-        for (auto &L : h->lv) {
-            if (&L == &h->lv.front() && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
+        const int cap = stage_capacity(fp32);
+        for (int k = 0; k < nlev; k++) {
+            LevelData &L = h->lv[k];
+            if (k == 0 && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
             if (small_level_fits(level_view(L), fp32)) continue;
             const int hv[2] = {0, L.n};
             CMG_CUDA(cudaMemcpyAsync(voff1, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
             CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, fp32,
                                        &L.lay, &lay_bytes, s));
             L.has_lay = true;
+            // gathers that a staged prefix of the iterate would serve
+            stage_try[k] = std::min(L.n, cap);
+            if (stage_try[k] > 0) CMG_TRY(layout_count_below(L.lay, stage_try[k], below_dev + k, s));
         }
     }
     // ---- solve workspace: a buffer pair per level, results, barrier state
@@ -372,7 +383,23 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     }
     bytes += sizeof(double) * (size_t)n;
     h->bytes = bytes + lay_bytes;
+    bool any_stage = false;
+    for (int k = 0; k < nlev; k++) any_stage = any_stage || stage_try[k] > 0;
+    if (any_stage)
+        CMG_CUDA(cudaMemcpyAsync(below.data(), below_dev, sizeof(unsigned long long) * (size_t)nlev,
+                                 cudaMemcpyDeviceToHost, s));
     CMG_CUDA(cudaStreamSynchronize(s));
+    if (any_stage) {
+        // CMG_STAGE=0: never stage the iterate; CMG_STAGE=1: stage it on every
+        // level with a sweep layout; otherwise where stage_pays() says so
+        const char *env = getenv("CMG_STAGE");
+        const int mode = (env && env[0] == '0') ? 0 : ((env && env[0] == '1') ? 1 : 2);
+        DeviceInfo di;
+        CMG_TRY(device_info(&di));
+        for (int k = 0; k < nlev; k++)
+            if (stage_try[k] > 0 && (mode == 1 || (mode == 2 && stage_pays(below[k], h->lv[k].lay.entries, di.sms))))
+                h->lv[k].lay.stage_n = stage_try[k];
+    }
     return CMG_OK;
 }
 
@@ -551,6 +578,21 @@ cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_p
     for (size_t j = 0; j < h->lv.size(); j++) {
         if (n_per_level) n_per_level[j] = h->lv[j].n;
         if (nnz_per_level) nnz_per_level[j] = h->lv[j].nnz;
+    }
+    return CMG_OK;
+}
+
+cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *staged_out) {
+    if (!h) return CMG_ERR_INVALID_ARG;
+    const int fp32 = h->opts.precision == CMG_PRECISION_FP32_SWEEP;
+    for (size_t j = 0; j < h->lv.size(); j++) {
+        const LevelData &L = h->lv[j];
+        const int staged = L.has_lay ? L.lay.stage_n : 0;
+        int kind = 0;
+        if (L.has_lay) kind = staged > 0 ? 2 : 1;
+        else if (!small_level_fits(level_view(L), fp32)) kind = 3;
+        if (kind_out) kind_out[j] = kind;
+        if (staged_out) staged_out[j] = staged;
     }
     return CMG_OK;
 }

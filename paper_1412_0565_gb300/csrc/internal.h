@@ -77,12 +77,16 @@ struct SweepLayout {
     int col16 = 1;
     long long entries = 0;
     std::vector<int> hecnt, hmcnt, hheavy;   // per graph, host copies
-    // single-graph layouts: heavy rows cut into chunks of kHeavyChunk entries
+    // single-graph layouts: heavy rows (stored padded to a multiple of 8
+    // entries) cut into chunks of at most kHeavyChunk entries
     int *hchunk = nullptr;      // [h+1] first chunk of each heavy row
     int *crow = nullptr;        // [nchunks] heavy row of each chunk
     int *hcount = nullptr;      // [h] chunks finished (zeroed per launch)
     void *cpart = nullptr;      // [nchunks] chunk partial sums (sweep precision)
     int nchunks = 0;
+    // single-graph layouts: iterate entries the slice kernel stages in shared
+    // memory per sweep (0: none)
+    int stage_n = 0;
 };
 constexpr int kHeavyChunk = 2048;
 // Builds the layout of the N rows of a level holding G graphs at union
@@ -92,6 +96,18 @@ cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &
                                 const int *rp, const int *col, const double *w, int fp32,
                                 SweepLayout *L, size_t *bytes, cudaStream_t s);
 void free_sweep_layout(SweepLayout &L, cudaStream_t s);
+// Adds to *out (zeroed first) the layout entries whose column is below S.
+cmg_status_t layout_count_below(const SweepLayout &L, int S, unsigned long long *out, cudaStream_t s);
+// Iterate entries the staged slice kernel can hold in shared memory (FP32 or
+// FP64 sweeps).
+int stage_capacity(int fp32);
+// Staging pays when the staged prefix serves nearly all gathers of a sweep
+// (`below` of the layout's `entries`; the large shared-memory carve-out
+// leaves little L1 for the other gathers and for loads in flight) and a sweep
+// holds enough gathers per SM to repay the copy.
+inline bool stage_pays(unsigned long long below, long long entries, int sms) {
+    return entries >= 16384ll * sms && below * 10ull >= (unsigned long long)entries * 9ull;
+}
 
 // Bits needed for the ids 0..c-1 (at least 1).
 inline int bits_for(int c) {

@@ -76,7 +76,8 @@ __device__ __forceinline__ int find_graph(const int *off, int G, int x) {
     return lo;
 }
 
-// Item sizes (one thread per renumbered row): a heavy row's entries, or for
+// Item sizes (one thread per renumbered row): a heavy row's entries rounded
+// up to a multiple of 8 (padding: weight 0, the row's own column), or for
 // the first row of a slice the slice's 32 x its longest row; a final item of
 // size 0 per graph.
 __global__ void k_layout_items(int n, int G, const int *__restrict__ voff, const int *__restrict__ rp,
@@ -87,7 +88,7 @@ __global__ void k_layout_items(int n, int G, const int *__restrict__ voff, const
         const int v0 = voff[q], ng = voff[q + 1] - v0, r = p - v0, h = heavy[q];
         int *it = items + moff[q];
         if (r < h) {
-            it[r] = perm_deg(rp, perm, p);
+            it[r] = (perm_deg(rp, perm, p) + 7) & ~7;   // 8-entry aligned, for vector loads
         } else if (((r - h) & 31) == 0) {
             it[h + ((r - h) >> 5)] = 32 * perm_deg(rp, perm, p);
         }
@@ -137,6 +138,10 @@ __global__ void k_layout_fill(int n, int G, const int *__restrict__ voff, const 
             for (int j = 0; j < deg; j++) {
                 gc[d0 + j] = (IDX)(inv[col[e0 + j]] - v0);
                 gw[d0 + j] = (T)w[e0 + j];
+            }
+            for (int j = deg; j < m[r + 1] - d0; j++) {   // padding to a multiple of 8
+                gc[d0 + j] = (IDX)r;
+                gw[d0 + j] = (T)0;
             }
             continue;
         }
@@ -277,6 +282,29 @@ cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &
     }
     if (bytes) *bytes += (size_t)N * 8 + (size_t)G * 12 + (size_t)tm * 4 + (size_t)te * (isz + esz);
     return CMG_OK;
+}
+
+// Layout entries (slice padding included: it is gathered too) whose column
+// is below S, added to *out.
+template <typename IDX>
+__global__ void k_count_below(long long m, const IDX *__restrict__ bcol, int S,
+                              unsigned long long *__restrict__ out) {
+    unsigned long long c = 0;
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < m; k += (long long)gridDim.x * blockDim.x)
+        c += ((int)bcol[k] < S) ? 1ull : 0ull;
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(out, c);
+}
+
+cmg_status_t layout_count_below(const SweepLayout &L, int S, unsigned long long *out, cudaStream_t s) {
+    CMG_CUDA(cudaMemsetAsync(out, 0, sizeof(unsigned long long), s));
+    if (L.entries <= 0) return CMG_OK;
+    const int blocks = (int)std::min<long long>(4096, (L.entries + 255) / 256);
+    if (L.col16)
+        k_count_below<<<blocks, 256, 0, s>>>(L.entries, (const uint16_t *)L.bcol, S, out);
+    else
+        k_count_below<<<blocks, 256, 0, s>>>(L.entries, (const int *)L.bcol, S, out);
+    return launch_status();
 }
 
 void free_sweep_layout(SweepLayout &L, cudaStream_t s) {

@@ -170,4 +170,84 @@ __device__ __forceinline__ T row_sum_grouped(const IDX *C, const T *W, int f0, i
     return a0 + a1;
 }
 
+// Eight consecutive layout entries from an index that is a multiple of 8
+// (16-byte aligned vectors); stream: evict-first loads.
+__device__ __forceinline__ void load_cols8(const uint16_t *C, int f, int (&cc)[8], bool stream) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(C + f);
+    const uint4 v = stream ? __ldcs(p) : *p;
+    const unsigned u[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        cc[2 * k] = (int)(u[k] & 0xffffu);
+        cc[2 * k + 1] = (int)(u[k] >> 16);
+    }
+}
+__device__ __forceinline__ void load_cols8(const int *C, int f, int (&cc)[8], bool stream) {
+    const int4 *p = reinterpret_cast<const int4 *>(C + f);
+    const int4 a = stream ? __ldcs(p) : p[0];
+    const int4 b = stream ? __ldcs(p + 1) : p[1];
+    cc[0] = a.x; cc[1] = a.y; cc[2] = a.z; cc[3] = a.w;
+    cc[4] = b.x; cc[5] = b.y; cc[6] = b.z; cc[7] = b.w;
+}
+__device__ __forceinline__ void load_w8(const float *W, int f, float (&ww)[8], bool stream) {
+    const float4 *p = reinterpret_cast<const float4 *>(W + f);
+    const float4 a = stream ? __ldcs(p) : p[0];
+    const float4 b = stream ? __ldcs(p + 1) : p[1];
+    ww[0] = a.x; ww[1] = a.y; ww[2] = a.z; ww[3] = a.w;
+    ww[4] = b.x; ww[5] = b.y; ww[6] = b.z; ww[7] = b.w;
+}
+__device__ __forceinline__ void load_w8(const double *W, int f, double (&ww)[8], bool stream) {
+    const double2 *p = reinterpret_cast<const double2 *>(W + f);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const double2 v = stream ? __ldcs(p + k) : p[k];
+        ww[2 * k] = v.x;
+        ww[2 * k + 1] = v.y;
+    }
+}
+
+// The sum of row_sum_grouped over a run of whole octets (8 entries from a
+// multiple of 8): octets o0, o0 + 32, ... < o1 belong to this lane, which
+// loads each with vector loads and takes OCT octets per round trip.
+template <typename T, typename IDX, int OCT, typename LD>
+__device__ __forceinline__ T row_sum_octets(const IDX *C, const T *W, int o0, int o1, T xi, LD ld,
+                                            bool stream) {
+    T a0 = (T)0, a1 = (T)0;
+    for (int o = o0; o < o1; o += 32 * OCT) {
+        int cc[OCT][8];
+        T ww[OCT][8];
+#pragma unroll
+        for (int v = 0; v < OCT; v++) {
+            if (o + 32 * v < o1) {
+                load_cols8(C, 8 * (o + 32 * v), cc[v], stream);
+                load_w8(W, 8 * (o + 32 * v), ww[v], stream);
+            } else {
+#pragma unroll
+                for (int u = 0; u < 8; u++) {
+                    cc[v][u] = -1;
+                    ww[v][u] = (T)0;
+                }
+            }
+        }
+        T xx[OCT][8];
+#pragma unroll
+        for (int v = 0; v < OCT; v++)
+#pragma unroll
+            for (int u = 0; u < 8; u++) xx[v][u] = (cc[v][u] >= 0) ? ld(cc[v][u]) : xi;
+#pragma unroll
+        for (int v = 0; v < OCT; v++)
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (sizeof(T) == 8) {
+                    if (u & 1) a1 = fma(ww[v][u], xx[v][u], a1);
+                    else a0 = fma(ww[v][u], xx[v][u], a0);
+                } else {
+                    if (u & 1) a1 += ww[v][u] * (xi - xx[v][u]);
+                    else a0 += ww[v][u] * (xi - xx[v][u]);
+                }
+            }
+    }
+    return a0 + a1;
+}
+
 }  // namespace cmg

@@ -62,6 +62,11 @@ __device__ long long g_trace[256][8];
 #endif
 
 constexpr int kTileThreads = 512;                 // warp 0: control, 15 row warps
+constexpr int kStageThreads = 1024;               // slice kernel with a staged iterate
+#ifndef CMG_OCT32
+#define CMG_OCT32 2
+#endif
+constexpr int kOct32 = CMG_OCT32;                 // FP32 heavy rows: octets per lane per round trip
 constexpr int kRowThreads = kTileThreads - 32;
 constexpr int kU = 8;                             // entries per row thread per chunk
 constexpr int kChunk = kRowThreads * kU;          // 3840 entries
@@ -108,6 +113,7 @@ struct PiArgs {
     void *cpart;            // chunk partial sums
     int nchunks;
     int stream_hint;        // the layout is larger than L2: read it evict-first
+    int stage_n;            // iterate entries 0..stage_n-1 copied to shared memory per sweep
 };
 
 
@@ -547,9 +553,19 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
 // per row; entry k of the slice's rows is one coalesced load), so the loads of
 // a sweep do not wait on one another and no CTA barrier is needed inside a
 // sweep.  The iterates are stored in layout order.
-template <typename T, typename IDX, bool CHUNKS, bool STREAM>
-__global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSync *gs) {
-    __shared__ Part s_pw[kTileThreads / 32];
+//
+// STAGE: one 1024-thread CTA per SM; at the top of each sweep the row warps
+// copy the iterate's first stage_n entries (the highest-degree rows, which
+// take the largest share of the gathers) into shared memory and gather from
+// there.  A gather of 32 scattered words from L1 or L2 costs about one cycle
+// per distinct line; from shared memory it costs the bank conflicts, a few
+// cycles per 32 words.
+template <typename T, typename IDX, bool CHUNKS, bool STREAM, bool STAGE>
+__global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 1 : 2)
+    k_power_sell(PiArgs a, GridSync *gs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const s_x = reinterpret_cast<T *>(smem_raw);
+    __shared__ Part s_pw[kStageThreads / 32];
     __shared__ Slot s_slot[2];
     const int n = a.n;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -649,7 +665,9 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSy
     int s = 0;
     int exit_kind = no_sweeps ? 2 : 0;
     const int rw = warp - 1, nrw = (int)(blockDim.x >> 5) - 1;            // row warps of this CTA
-    const int gw = blockIdx.x * nrw + rw, ngw = (int)gridDim.x * nrw;     // over the grid
+    // heavy-row chunks are dealt CTA by CTA (chunk k to CTA k mod grid), so
+    // a level with few chunks still spreads them over all SMs
+    const int gw = rw * (int)gridDim.x + blockIdx.x, ngw = (int)gridDim.x * nrw;
     while (!no_sweeps) {
         const Slot sl = s_slot[(s + 1) & 1];
         if (sl.stop) {
@@ -692,37 +710,76 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_sell(PiArgs a, GridSy
                 y[i] = yv;
                 acc.add(yv, xi);
             };
-            auto ldx = [&](int c) { return LDXG(x + c); };
-            // heavy rows: cut into chunks of kHeavyChunk entries, a warp per
-            // chunk; the warp that finishes a row's last chunk sums the row's
-            // chunk partials in chunk order and completes the row
+            const int S = STAGE ? a.stage_n : 0;
+            if (STAGE) {
+                // 16-byte copies of x[0, S) into shared memory, then the row
+                // warps meet (the control warp does not take part)
+                const int nrt = (int)blockDim.x - 32;
+                const int nv = ((reinterpret_cast<uintptr_t>(x) & 15) == 0) ? (int)(((long long)S * sizeof(T)) / 16) : 0;
+                const float4 *src = reinterpret_cast<const float4 *>(x);
+                float4 *dst = reinterpret_cast<float4 *>(s_x);
+                for (int k = tid - 32; k < nv; k += nrt) dst[k] = __ldcg(src + k);
+                for (int k = nv * (16 / (int)sizeof(T)) + tid - 32; k < S; k += nrt) s_x[k] = __ldcg(x + k);
+                bar_rows(nrt);
+            }
+            auto ldx = [&](int c) { return (STAGE && c < S) ? s_x[c] : LDXG(x + c); };
+            // heavy rows: a row of len entries (a multiple of 8) is cut into
+            // nc = ceil(len / kHeavyChunk) chunks of equal length rounded up
+            // to whole octets, a warp per chunk, lanes taking octets; the
+            // warp of a row's last chunk waits for the row's other chunks,
+            // sums the chunk partials in chunk order and completes the row
+            const bool vec = ((reinterpret_cast<uintptr_t>(C) | reinterpret_cast<uintptr_t>(W)) & 15) == 0;
             for (int cidx = gw; CHUNKS && cidx < a.nchunks; cidx += ngw) {
                 const int r = a.crow[cidx], c0 = a.hchunk[r], nc = a.hchunk[r + 1] - c0;
-                const int f0 = M[r] + (cidx - c0) * kHeavyChunk;
-                const int f1 = min(M[r + 1], f0 + kHeavyChunk);
-                const T xi = LDXG(x + r);
-                T ac = row_sum_grouped<T, IDX>(C, W, f0 + lane, f1, 32, xi, ldx, STREAM);
+                const int len = M[r + 1] - M[r];
+                const int per = (((len + nc - 1) / nc) + 7) & ~7;
+                const int f0 = min(M[r + 1], M[r] + (cidx - c0) * per);
+                const int f1 = min(M[r + 1], f0 + per);
+                const T xi = ldx(r);
+                T ac = vec ? row_sum_octets<T, IDX, sizeof(T) == 4 ? kOct32 : 1>(C, W, (f0 >> 3) + lane, f1 >> 3, xi, ldx,
+                                                                        STREAM)
+                           : row_sum_grouped<T, IDX>(C, W, f0 + lane, f1, 32, xi, ldx, STREAM);
                 ac = warp_sum(ac);
                 if (nc == 1) {
                     if (lane == 0) finish(r, xi, ac);
                 } else if (lane == 0) {
+                    // the warp of the row's last chunk completes the row (a
+                    // fixed thread, so the sweep's partial sums group the
+                    // same way in every run); the others publish their partial
                     T *cp = reinterpret_cast<T *>(a.cpart);
-                    cp[cidx] = ac;
-                    __threadfence();
-                    const int done = atomicAdd(a.hcount + r, 1);
-                    if (done == (s + 1) * nc - 1) {
-                        __threadfence();
+                    unsigned int *cnt = reinterpret_cast<unsigned int *>(a.hcount + r);
+                    if (cidx < c0 + nc - 1) {
+                        cp[cidx] = ac;
+                        red_add_release_gpu(cnt, 1u);
+                    } else {
+                        // the other chunks have lower indices: their warps
+                        // never wait on this one, so the wait ends; bounded
+                        // all the same (GridSync::err, like a barrier)
+                        const unsigned int want = (unsigned int)((s + 1) * (nc - 1));
+                        unsigned long long t0 = 0;
+                        for (unsigned int spin = 0; ld_acquire_gpu(cnt) < want; spin++) {
+                            if ((spin & 255u) == 255u) {
+                                const unsigned long long t = global_ns();
+                                if (t0 == 0) {
+                                    t0 = t;
+                                } else if (t - t0 > kBarrierTimeoutNs || ld_relaxed_gpu(&gs->err)) {
+                                    atomicExch(&gs->err, 1u);
+                                    break;
+                                }
+                            }
+                        }
                         T tot = (T)0;
-                        for (int c = c0; c < c0 + nc; c++) tot += __ldcg(cp + c);
-                        finish(r, xi, tot);
+                        for (int c = c0; c < c0 + nc - 1; c++) tot += __ldcg(cp + c);
+                        finish(r, xi, tot + ac);
                     }
                 }
+                __syncwarp();
             }
             // slices: a lane per row, entries in groups of 8 (row_sum_grouped)
             for (int q = sb + rw; q < se; q += nrw) {
                 const int i = h + 32 * q + lane;
                 const int so = SO[q] + lane, wd = (SO[q + 1] - SO[q]) >> 5;
-                const T xi = (i < n) ? LDXG(x + i) : (T)0;
+                const T xi = (i < n) ? ldx(i) : (T)0;
                 const T ac = row_sum_grouped<T, IDX>(C, W, so, so + 32 * wd, 32, xi, ldx, STREAM);
                 if (i < n) finish(i, xi, ac);
             }
@@ -1050,15 +1107,26 @@ static size_t tiled_smem(bool fp32) {
     return ts + e * 2 * kTileRows + sizeof(int) * (kTileRows + 4) + 2 * kChunk;
 }
 
-template <typename T, typename IDX>
-static const void *sell_kernel_ti(bool chunks, bool stream) {
-    if (chunks) return stream ? (const void *)k_power_sell<T, IDX, true, true> : (const void *)k_power_sell<T, IDX, true, false>;
-    return stream ? (const void *)k_power_sell<T, IDX, false, true> : (const void *)k_power_sell<T, IDX, false, false>;
+template <typename T, typename IDX, bool STAGE>
+static const void *sell_kernel_tis(bool chunks, bool stream) {
+    if (chunks)
+        return stream ? (const void *)k_power_sell<T, IDX, true, true, STAGE>
+                      : (const void *)k_power_sell<T, IDX, true, false, STAGE>;
+    return stream ? (const void *)k_power_sell<T, IDX, false, true, STAGE>
+                  : (const void *)k_power_sell<T, IDX, false, false, STAGE>;
 }
 
-static const void *sell_kernel(int fp32, int col16, bool chunks, bool stream) {
-    if (fp32) return col16 ? sell_kernel_ti<float, uint16_t>(chunks, stream) : sell_kernel_ti<float, int>(chunks, stream);
-    return col16 ? sell_kernel_ti<double, uint16_t>(chunks, stream) : sell_kernel_ti<double, int>(chunks, stream);
+template <typename T, typename IDX>
+static const void *sell_kernel_ti(bool chunks, bool stream, bool stage) {
+    return stage ? sell_kernel_tis<T, IDX, true>(chunks, stream) : sell_kernel_tis<T, IDX, false>(chunks, stream);
+}
+
+static const void *sell_kernel(int fp32, int col16, bool chunks, bool stream, bool stage) {
+    if (fp32)
+        return col16 ? sell_kernel_ti<float, uint16_t>(chunks, stream, stage)
+                     : sell_kernel_ti<float, int>(chunks, stream, stage);
+    return col16 ? sell_kernel_ti<double, uint16_t>(chunks, stream, stage)
+                 : sell_kernel_ti<double, int>(chunks, stream, stage);
 }
 
 template <typename T>
@@ -1108,6 +1176,19 @@ static long long small_entries(const PiLevel &lv, int G) {
 static size_t small_bytes(const PiLevel &lv, int G, int fp32) {
     const long long e = small_entries(lv, G);
     return fp32 ? small_smem_bytes<float>(lv.n, e) : small_smem_bytes<double>(lv.n, e);
+}
+
+int stage_capacity(int fp32) {
+    DeviceInfo d;
+    if (device_info(&d) != CMG_OK) return 0;
+    cudaFuncAttributes fa;
+    const void *k = fp32 ? (const void *)k_power_sell<float, int, true, true, true>
+                         : (const void *)k_power_sell<double, int, true, true, true>;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
+    const long long room = (long long)d.max_smem_optin - (long long)fa.sharedSizeBytes - 256;
+    if (room <= 0) return 0;
+    const long long cap = room / (fp32 ? (long long)sizeof(float) : (long long)sizeof(double));
+    return (int)(cap & ~3ll);
 }
 
 bool small_level_fits(const PiLevel &lv, int fp32) {
@@ -1188,6 +1269,7 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.cpart = nullptr;
     a.nchunks = 0;
     a.stream_hint = 0;
+    a.stage_n = 0;
     void *args[] = {&a, &gs};
     if (small_level_fits(lv, run.fp32)) {
         const int G = small_lanes(lv.n, lv.nnz, run.fp32);
@@ -1224,10 +1306,15 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
             if (!L.hchunk) return CMG_ERR_INVALID_ARG;
             CMG_CUDA(cudaMemsetAsync(L.hcount, 0, sizeof(int) * (size_t)a.lay_h, s));
         }
-        const void *kern = sell_kernel(run.fp32, L.col16, a.lay_h > 0, a.stream_hint != 0);
+        a.stage_n = std::min(L.stage_n, lv.n);
+        const bool stage = a.stage_n > 0;
+        const void *kern = sell_kernel(run.fp32, L.col16, a.lay_h > 0, a.stream_hint != 0, stage);
+        const int threads = stage ? kStageThreads : kTileThreads;
+        const size_t smem = stage ? (size_t)a.stage_n * (run.fp32 ? sizeof(float) : sizeof(double)) : 0;
+        if (stage) CMG_TRY(allow_max_dynamic_smem(kern));
         int maxb = 0;
-        CMG_TRY(coop_max_blocks(kern, kTileThreads, 0, &maxb));
-        const int row_warps = kTileThreads / 32 - 1;
+        CMG_TRY(coop_max_blocks(kern, threads, smem, &maxb));
+        const int row_warps = threads / 32 - 1;
         const long long tasks = (long long)a.lay_nsl + a.nchunks;
         const int blocks = (int)std::max<long long>(1, std::min<long long>(maxb, (tasks + row_warps - 1) / row_warps));
         double *partials;
@@ -1238,7 +1325,7 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
             CMG_TRY(scr.get(&partials, (size_t)2 * blocks * 3));
         }
         a.partials = reinterpret_cast<ff *>(partials);
-        return coop_launch(kern, blocks, kTileThreads, 0, s, args, gs);
+        return coop_launch(kern, blocks, threads, smem, s, args, gs);
     }
     if (!a.tile_row) {
         int *tr;

@@ -165,3 +165,59 @@ def test_full_size_3d_grid_matches_oracle():
     assert st["sweeps"] == ref["sweeps"].tolist()
     assert aligned_err(u, ref_u) <= VEC_TOL
     assert abs(lam - ref_lam) <= LAM_TOL * abs(ref_lam)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_staged_iterate_kernel_matches_oracle(monkeypatch, precision):
+    """The slice kernel that stages the iterate's highest-degree prefix in
+    shared memory, forced on every slice level, against the oracle; also the
+    same solve with staging off.  (The two launch different CTA counts, so
+    their float-float partial sums group differently: they agree within the
+    parity tolerances, not bit for bit.)  70,000 vertices: the staged prefix
+    (about 57,000 FP32 or 28,500 FP64 entries) is shorter than level 0, so
+    both gather paths run."""
+    rp, col, w = inputs.chung_lu(70000, seed=11)
+    assert len(rp) - 1 > 57344
+    oh = oracle.Hierarchy(rp, col, w, seed=1412)
+    ref64 = oh.solve()
+    for mode in ("1", "0"):
+        monkeypatch.setenv("CMG_STAGE", mode)
+        h = cmg.Hierarchy(rp, col, w, seed=1412, precision=precision)
+        kind, staged = h.level_kernels()
+        if mode == "0":
+            assert 2 not in kind and not any(staged)
+        else:
+            assert kind[0] == 2 and 0 < staged[0] < len(rp) - 1
+            assert all((k == 2) == (s > 0) for k, s in zip(kind, staged))
+            assert 1 not in kind
+        u, lam, st = h.fiedler()
+        for _ in range(2):
+            u2, lam2, _ = h.fiedler()
+            assert np.array_equal(u, u2) and lam == lam2
+        h.close()
+        if precision == "fp64":
+            assert st["sweeps"] == ref64["sweeps"].tolist()
+            assert aligned_err(u, ref64["u"]) <= VEC_TOL
+            assert abs(lam - ref64["lam"]) <= LAM_TOL * abs(ref64["lam"])
+        else:
+            ref = oh.solve(schedule="replay", replay=st["sweeps"])
+            assert abs(lam - ref["lam"]) <= 1e-6 * abs(ref["lam"])
+            assert angle(u, ref["u"]) <= 1e-4
+    monkeypatch.delenv("CMG_STAGE")
+
+
+def test_stage_rule_picks_dense_power_law_levels():
+    """Without the override, staging is chosen where gathers are many per
+    staged entry: the dense coarse levels of a power-law graph, not the
+    levels of a 3-D grid."""
+    # levels of this graph: 399,708 / 105,389 / 25,604 / 6,072 / 1,088 rows
+    # with 6.4M / 5.7M / 5.3M / 3.8M / 0.65M stored entries
+    h = cmg.Hierarchy(*inputs.chung_lu(400000, seed=12), seed=1412, precision="fp32")
+    kind, staged = h.level_kernels()
+    assert kind[0] == 1 and staged[0] == 0       # a short prefix of a long iterate
+    assert kind[2] == 2 and staged[2] == 25604   # the whole iterate, 5.3M gathers a sweep
+    h.close()
+    h = cmg.Hierarchy(*inputs.grid3d(60, 60, 60, "uniform", seed=1), seed=1412, precision="fp32")
+    kind, staged = h.level_kernels()
+    assert 2 not in kind and 1 in kind
+    h.close()
