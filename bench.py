@@ -516,8 +516,9 @@ def run_batch(args, stream, flush):
     return res
 
 
-CL_WORKLOAD = ("Chung-Lu power-law graph, n 4,194,304 before the largest component, mean degree 16, "
-               "exponent 2.5, degrees capped at sqrt(16 n), lognormal(0,1) weights, seed 1412")
+def cl_workload(n):
+    return (f"Chung-Lu power-law graph, n {n:,} before the largest component, mean degree 16, "
+            "exponent 2.5, degrees capped at sqrt(16 n), lognormal(0,1) weights, seed 1412")
 
 
 def run_chung_lu(args, stream, flush):
@@ -526,14 +527,14 @@ def run_chung_lu(args, stream, flush):
     import torch
     from paper_1412_0565_gb300 import cmg, inputs
     t0 = time.perf_counter()
-    rp, col, w = inputs.chung_lu(4_194_304, seed=1412)
+    rp, col, w = inputs.chung_lu(args.cl_n, seed=1412)
     gen_s = time.perf_counter() - t0
     n, nnz = len(rp) - 1, int(rp[-1])
     sid = stream.cuda_stream
     drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
     u = torch.empty(n, dtype=torch.float64, device="cuda")
     deg = rp[1:] - rp[:-1]
-    out = {"workload": CL_WORKLOAD, "n": n, "nnz": nnz, "max_degree": int(deg.max()),
+    out = {"workload": cl_workload(args.cl_n), "n": n, "nnz": nnz, "max_degree": int(deg.max()),
            "generate_s": round(gen_s, 1)}
     res = {}
     for prec in ("fp32", "fp64"):
@@ -664,6 +665,8 @@ def main():
     ap.add_argument("--no-chung-lu", action="store_true")
     ap.add_argument("--cl-steps", type=int, default=3)
     ap.add_argument("--cl-warmup", type=int, default=1)
+    ap.add_argument("--cl-n", type=int, default=4_194_304,
+                    help="Chung-Lu vertices before the largest component (smaller: profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
