@@ -67,6 +67,7 @@ def test_host_side_argument_errors_need_no_gpu():
     assert cmg.STATUS[st] == "ERR_INVALID_ARG"
     assert cmg.STATUS[lib.cmg_fiedler(None, None, 0, None, None, None)] == "ERR_INVALID_ARG"
     assert cmg.STATUS[lib.cmg_free(None)] == "ERR_INVALID_ARG"
+    assert cmg.STATUS[lib.cmg_level_kernels(None, None, None)] == "ERR_INVALID_ARG"
 
 
 def test_estimate_device_bytes_monotone():
