@@ -309,15 +309,22 @@ def run_gpu(args):
 
     # ---- end to end through the public API with host buffers (FP32 form)
     e2e_ms = []
-    hu = np.empty(n, dtype=np.float64)
-    rp_h = np.ascontiguousarray(rp)
+    # inputs and the result buffer in pinned host memory (filled once, outside
+    # the timed region), so the copies inside it are plain DMA transfers
+    try:
+        rp_h, col_h, w_h, hu = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+                                for a in (rp, col, w, np.empty(n, dtype=np.float64)))
+        pinned = True
+    except Exception:
+        rp_h, col_h, w_h, hu = (np.ascontiguousarray(a) for a in (rp, col, w, np.empty(n, dtype=np.float64)))
+        pinned = False
     for _ in range(max(2, min(args.steps, 5))):
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        h = cmg.Hierarchy(rp_h, col, w, seed=1412, precision="fp32", stream=sid)
+        h = cmg.Hierarchy(rp_h, col_h, w_h, seed=1412, precision="fp32", stream=sid)
         h.fiedler(u_out=hu, stream=sid)
         h.close()
         e1.record(stream)
@@ -379,7 +386,8 @@ def run_gpu(args):
             "fp32_vs_fp64": acc,
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n},
+                    "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n,
+                    "host_memory": "pinned" if pinned else "pageable"},
             "gpu_launches": r32["launches"],
             "clocks": clocks,
             "batch": batch,
