@@ -150,6 +150,24 @@ def cpu_info():
     return model or os.uname().machine
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest value over the ranks of the job (each rank's timed total:
+    the job takes as long as its slowest replica)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, total_ms: float, world: int, device: str = "cuda") -> float:
+    """Units all ranks processed (each rank the same count: replicas) per
+    second of the slowest rank's timed total."""
+    return world * units_per_rank / (max_over_ranks(total_ms, world, device) / 1e3)
+
+
 def oracle_solve(rp, col, w):
     import oracle
     h = oracle.Hierarchy(rp, col, w, seed=1412)
@@ -249,11 +267,7 @@ def run_gpu(args):
             stats.append(st)
         barrier()
         launches = cmg.kernel_launches() - l0
-        total = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total = float(t.item())
+        total = max_over_ranks(sum(step_ms), world)
         srt = sorted(step_ms)
         return {"value": world * steps / (total / 1e3), "ms_per_step": total / steps,
                 "p50_ms": srt[len(srt) // 2], "p99_ms": srt[min(len(srt) - 1, int(0.99 * len(srt)))],
@@ -330,12 +344,7 @@ def run_gpu(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_tot = sum(e2e_ms)
-    if world > 1:
-        t = torch.tensor([e2e_tot], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_tot = float(t.item())
-    e2e_val = world * len(e2e_ms) / (e2e_tot / 1e3)
+    e2e_val = whole_job_rate(len(e2e_ms), sum(e2e_ms), world)
 
     batch = None
     if not args.no_batch and world == 1:
