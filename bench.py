@@ -121,16 +121,30 @@ PROFILED_SOURCES = [os.path.join(ROOT, "paper_1412_0565_gb300", "csrc", f)
                     for f in ("refine.cu", "pi_common.cuh", "ffloat.cuh")]
 
 
+def kernel_fingerprint():
+    """sha256 (16 hex digits) of the profiled kernel sources with comments and
+    whitespace removed: a comment edit keeps the capture valid, a code edit
+    does not."""
+    import hashlib
+    import re
+    parts = []
+    for f in PROFILED_SOURCES:
+        src = open(f).read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        parts.append(" ".join(src.split()))
+    return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per level-0 launch from the committed ncu summary, or None
-    when the kernel sources changed since that capture."""
-    import hashlib
+    when the kernel code changed since that capture."""
     try:
         text = open(PROFILE).read()
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in PROFILED_SOURCES)).hexdigest()[:16]
+        h = kernel_fingerprint()
         fields = dict(line.strip("- ").split(": ", 1) for line in text.splitlines()
                       if line.startswith("- ") and ": " in line)
-        if fields.get("kernel_source_sha256_16") != h:
+        if fields.get("kernel_code_sha256_16") != h:
             return None, "kernel changed since the ncu capture"
         return int(fields["traffic_bytes_per_launch"]), "dram read+write per launch, ncu (profiles/)"
     except Exception as e:  # missing or malformed summary

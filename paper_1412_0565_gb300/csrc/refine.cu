@@ -549,10 +549,10 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
 // Large levels with a sweep layout (rows renumbered by decreasing degree;
 // heavy rows in CSR form, the rest in 32-row slices with interleaved entries):
 // cooperative persistent kernel with the control warp of k_power_tiled.  A
-// row warp takes a heavy row (32 lanes over its entries) or a slice (one lane
-// per row; entry k of the slice's rows is one coalesced load), so the loads of
-// a sweep do not wait on one another and no CTA barrier is needed inside a
-// sweep.  The iterates are stored in layout order.
+// row warp takes a chunk of a heavy row (32 lanes over its octets) or a slice
+// (one lane per row; entry k of the slice's rows is one coalesced load), so
+// the loads of a sweep do not wait on one another and no CTA barrier is
+// needed inside a sweep.  The iterates are stored in layout order.
 //
 // STAGE: one 1024-thread CTA per SM; at the top of each sweep the row warps
 // copy the iterate's first stage_n entries (the highest-degree rows, which
