@@ -117,6 +117,7 @@ class ClockSampler:
 
 
 PROFILE = os.path.join(ROOT, "profiles", "k_power_sell_f32_grid3d_100_level0.md")
+NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
 PROFILED_SOURCES = [os.path.join(ROOT, "paper_1412_0565_gb300", "csrc", f)
                     for f in ("refine.cu", "pi_common.cuh", "ffloat.cuh")]
 
@@ -323,6 +324,7 @@ def run_gpu(args):
     roof = {"bound": "hbm", "kernel": "k_power_sell<float, int>, level-0 launch",
             "achieved": achieved0, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
             "frac": achieved0 / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
+            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved0 / NOMINAL_HBM_GBS,
             "bytes_per_launch": by0,
             "launch_ms": ms0, "sweeps_per_launch": st32["sweeps"][0],
             "all_levels": {"bytes": tot_b, "ms": tot_ms, "achieved": tot_b / (tot_ms * 1e-3) / 1e9}}
