@@ -73,3 +73,17 @@ def test_reference_arm_runs_on_rank_zero_only():
                        timeout=120, cwd=ROOT)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""                      # no line, no work on other ranks
+
+
+def test_kernel_fingerprint_ignores_comments_only(tmp_path, monkeypatch):
+    """The profile's code hash survives comment and whitespace edits, not code edits."""
+    sys.path.insert(0, ROOT)
+    import bench
+    a = tmp_path / "a.cu"
+    a.write_text("// head\nint f(int x) { /* note */ return x + 1; }\n")
+    monkeypatch.setattr(bench, "PROFILED_SOURCES", [str(a)])
+    h0 = bench.kernel_fingerprint()
+    a.write_text("// another comment\nint f(int x)  {\n  return x + 1;  // trailing\n}\n")
+    assert bench.kernel_fingerprint() == h0
+    a.write_text("int f(int x) { return x + 2; }\n")
+    assert bench.kernel_fingerprint() != h0
