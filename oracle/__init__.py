@@ -86,6 +86,11 @@ def _load():
         lib.orc_solve.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_int32, C.c_double,
                                   C.c_int32, I64P, C.c_int64, C.c_int64, C.c_int32, C.c_double,
                                   F64P, F64P, F64P, I64P, F64P]
+        lib.orc_solve_ex.restype = C.c_int32
+        lib.orc_solve_ex.argtypes = [C.c_void_p, C.c_uint64, C.c_double, C.c_int32, C.c_double,
+                                     C.c_int32, I64P, C.c_int64, C.c_int64, C.c_int32,
+                                     C.c_double, C.c_int32, F64P, F64P, F64P, F64P, I64P, F64P,
+                                     F64P, F64P]
         _lib = lib
         return lib
 
@@ -229,26 +234,54 @@ class Hierarchy:
 
     def solve(self, *, tol=1e-8, schedule="tol", beta=4.0, k0=1, replay=None,
               max_sweeps=20000, max_sweeps_coarsest=100000, converged=False, conv_rtol=1e-11,
-              seed=None):
-        """Alg. 1 Steps 2-3.  Returns dict(u, lam, res, sweeps, cos, capped)."""
+              seed=None, start_level=None, x0=None, trace=False):
+        """Alg. 1 Steps 2-3.  Returns dict(u, lam, res, sweeps, cos, capped).
+
+        start_level / x0: start the cascade on that level from x0 (in the
+        level's numbering) instead of the Gaussian start on the coarsest level.
+        trace: also return "start" and "end", lists (one entry per level,
+        None for levels not visited) of the vector each level's power
+        iteration starts from (before Gram-Schmidt) and the one it returns."""
         J = self.levels - 1
-        n0 = self.info(0)[0]
+        sizes = self.sizes()
+        n0 = sizes[0]
         sched = {"tol": 0, "fixed": 1, "replay": 2}[schedule]
         rep = np.zeros(J + 1, dtype=np.int64)
         if replay is not None:
             rep[:] = np.asarray(replay, dtype=np.int64)[: J + 1]
+        sl = -1
+        xp = None
+        if start_level is not None:
+            sl = int(start_level)
+            if not 0 <= sl <= J:
+                raise ValueError("start_level out of range")
+            xp = np.ascontiguousarray(x0, dtype=np.float64)
+            if xp.shape != (sizes[sl],):
+                raise ValueError("x0 must have the start level's size")
         u = np.empty(n0, dtype=np.float64)
         lam = C.c_double()
         res = C.c_double()
         sweeps = np.zeros(J + 1, dtype=np.int64)
         cos = np.zeros(J + 1, dtype=np.float64)
-        warn = _load().orc_solve(self._h, C.c_uint64(self.seed if seed is None else seed),
-                                 float(tol), sched, float(beta), int(k0), _p(rep, C.c_int64),
-                                 int(max_sweeps), int(max_sweeps_coarsest), 1 if converged else 0,
-                                 float(conv_rtol), _p(u, C.c_double), C.byref(lam), C.byref(res),
-                                 _p(sweeps, C.c_int64), _p(cos, C.c_double))
-        return {"u": u, "lam": lam.value, "res": res.value, "sweeps": sweeps, "cos": cos,
-                "capped": bool(warn)}
+        tot = int(sum(sizes))
+        ts = np.full(tot, np.nan) if trace else None
+        te = np.full(tot, np.nan) if trace else None
+        nul = C.cast(None, F64P)
+        warn = _load().orc_solve_ex(
+            self._h, C.c_uint64(self.seed if seed is None else seed), float(tol), sched,
+            float(beta), int(k0), _p(rep, C.c_int64), int(max_sweeps), int(max_sweeps_coarsest),
+            1 if converged else 0, float(conv_rtol), sl,
+            _p(xp, C.c_double) if xp is not None else nul, _p(u, C.c_double), C.byref(lam),
+            C.byref(res), _p(sweeps, C.c_int64), _p(cos, C.c_double),
+            _p(ts, C.c_double) if trace else nul, _p(te, C.c_double) if trace else nul)
+        out = {"u": u, "lam": lam.value, "res": res.value, "sweeps": sweeps, "cos": cos,
+               "capped": bool(warn)}
+        if trace:
+            off = np.concatenate([[0], np.cumsum(sizes)])
+            top = J if sl < 0 else sl
+            out["start"] = [ts[off[j]:off[j + 1]].copy() if j <= top else None for j in range(J + 1)]
+            out["end"] = [te[off[j]:off[j + 1]].copy() if j <= top else None for j in range(J + 1)]
+        return out
 
 
 def fiedler(rp, col, w, *, seed=1412, tol=1e-8, coarse_size=25, **kw):

@@ -536,35 +536,72 @@ ORC_EXPORT void orc_free(orc_hierarchy *h)
  * schedule 2 (replay):    exactly replay[j] sweeps at level j (j = 0..J).
  * converged != 0: after level 0's sweeps, keep sweeping level 0 until
  *                 ||(L - lambda I) u|| <= conv_rtol * g_0 (test use only).
+ * start_level < 0: Step 2 from the Gaussian start keyed by `seed`, then Step 3.
+ * start_level = s in 0..J: the cascade starts on level s from x0 (length n_s,
+ *                 level s's numbering) instead: PI(L^s, x0), then Step 3 from
+ *                 level s-1 down to 0; levels above s are not visited (0 sweeps).
+ *                 This is the re-solve with a new start vector on a kept
+ *                 hierarchy that the Remark after Alg. 1 has in mind for
+ *                 repeated computations.
+ * trace_start, trace_end (nullable, length sum_j n_j, level j at offset
+ *                 n_0 + ... + n_{j-1}): the vector each visited level's PI
+ *                 starts from (the Gaussian, x0, or the prolongation
+ *                 (I_j^{j+1})^T y~^(j+1) before Gram-Schmidt) and the vector it
+ *                 returns, y~^(j) (before the sign rule).  Unvisited levels are
+ *                 left untouched.
  * Outputs: u (length n_0, R11 sign), lambda, residual, sweeps[j], cosines[j].
  * Returns 1 if a sweep cap was reached, else 0.                              */
-ORC_EXPORT int32_t orc_solve(orc_hierarchy *h, uint64_t seed, double tol, int32_t schedule,
-                             double beta, int32_t k0, const int64_t *replay,
-                             int64_t max_sweeps, int64_t max_sweeps_coarsest, int32_t converged,
-                             double conv_rtol, double *u, double *lambda_out,
-                             double *residual_out, int64_t *sweeps_out, double *cos_out)
+ORC_EXPORT int32_t orc_solve_ex(orc_hierarchy *h, uint64_t seed, double tol, int32_t schedule,
+                                double beta, int32_t k0, const int64_t *replay,
+                                int64_t max_sweeps, int64_t max_sweeps_coarsest,
+                                int32_t converged, double conv_rtol, int32_t start_level,
+                                const double *x0, double *u, double *lambda_out,
+                                double *residual_out, int64_t *sweeps_out, double *cos_out,
+                                double *trace_start, double *trace_end)
 {
     int32_t J = h->levels - 1;
     int32_t warn = 0;
-    /* Step 2: PI(L^J, randn(n_J)) */
-    orc_level *c = &h->lv[J];
+    int32_t top = (start_level >= 0 && start_level <= J) ? start_level : J;
+    int64_t off[65];
+    off[0] = 0;
+    for (int32_t j = 0; j <= J; j++) off[j + 1] = off[j] + h->lv[j].n;
+    for (int32_t j = top + 1; j <= J; j++) {
+        h->lv[j].sweeps = 0;
+        h->lv[j].cos_final = 0.0;
+    }
+    /* Step 2: PI(L^J, randn(n_J)), or PI(L^s, x0) for a given start */
+    orc_level *c = &h->lv[top];
     double *y = (double *)malloc(sizeof(double) * (size_t)c->n);
     double *yt = (double *)malloc(sizeof(double) * (size_t)c->n);
-    orc_gaussian_start(seed, c->n, y);
+    if (top == start_level)
+        memcpy(y, x0, sizeof(double) * (size_t)c->n);
+    else
+        orc_gaussian_start(seed, c->n, y);
+    if (trace_start) memcpy(trace_start + off[top], y, sizeof(double) * (size_t)c->n);
     int32_t capped = 0;
-    int32_t mode = (schedule == 2) ? 1 : 0;
-    int64_t kf = (schedule == 2) ? replay[J] : 0;
+    int32_t mode = 0;
+    int64_t kf = 0;
+    if (schedule == 2) {
+        mode = 1;
+        kf = replay[top];
+    } else if (schedule == 1 && top < J) {
+        mode = 1;
+        kf = (int64_t)ceil((double)k0 * pow(beta, (double)top));
+    }
     c->sweeps = orc_power_iteration(c->n, c->rp, c->col, c->w, c->g, y, tol, mode, kf,
-                                    max_sweeps_coarsest, yt, &c->cos_final, &capped);
+                                    top == J ? max_sweeps_coarsest : max_sweeps, yt,
+                                    &c->cos_final, &capped);
     warn |= capped;
+    if (trace_end) memcpy(trace_end + off[top], yt, sizeof(double) * (size_t)c->n);
     free(y);
     y = yt;
-    /* Step 3: for j = J-1 down to 0: prolongate, then PI */
-    for (int32_t j = J - 1; j >= 0; j--) {
+    /* Step 3: for j = top-1 down to 0: prolongate, then PI */
+    for (int32_t j = top - 1; j >= 0; j--) {
         orc_level *f = &h->lv[j];
         double *yh = (double *)malloc(sizeof(double) * (size_t)f->n);
         double *yn = (double *)malloc(sizeof(double) * (size_t)f->n);
         for (int64_t i = 0; i < f->n; i++) yh[i] = y[f->agg[i]]; /* (I_j^{j+1})^T y */
+        if (trace_start) memcpy(trace_start + off[j], yh, sizeof(double) * (size_t)f->n);
         int32_t md = 0;
         int64_t k = 0;
         if (schedule == 1) {
@@ -577,6 +614,7 @@ ORC_EXPORT int32_t orc_solve(orc_hierarchy *h, uint64_t seed, double tol, int32_
         f->sweeps = orc_power_iteration(f->n, f->rp, f->col, f->w, f->g, yh, tol, md, k,
                                         max_sweeps, yn, &f->cos_final, &capped);
         warn |= capped;
+        if (trace_end) memcpy(trace_end + off[j], yn, sizeof(double) * (size_t)f->n);
         free(yh);
         free(y);
         y = yn;
@@ -607,4 +645,17 @@ ORC_EXPORT int32_t orc_solve(orc_hierarchy *h, uint64_t seed, double tol, int32_
     }
     free(y);
     return warn;
+}
+
+/* Alg. 1 Steps 2-3 from the Gaussian start (orc_solve_ex without a given
+ * start vector and without traces).                                          */
+ORC_EXPORT int32_t orc_solve(orc_hierarchy *h, uint64_t seed, double tol, int32_t schedule,
+                             double beta, int32_t k0, const int64_t *replay,
+                             int64_t max_sweeps, int64_t max_sweeps_coarsest, int32_t converged,
+                             double conv_rtol, double *u, double *lambda_out,
+                             double *residual_out, int64_t *sweeps_out, double *cos_out)
+{
+    return orc_solve_ex(h, seed, tol, schedule, beta, k0, replay, max_sweeps, max_sweeps_coarsest,
+                        converged, conv_rtol, -1, NULL, u, lambda_out, residual_out, sweeps_out,
+                        cos_out, NULL, NULL);
 }

@@ -445,3 +445,125 @@ def test_fixed_and_replay_schedules():
     rr = h.solve(schedule="replay", replay=t["sweeps"])
     assert np.array_equal(rr["sweeps"], t["sweeps"])
     assert np.array_equal(rr["u"], t["u"])
+
+
+# ------------------------------------------------------------------ Alg. 1 Step 3: the cascade
+def _prolongation_matrix(agg, n_coarse):
+    """(I_j^{j+1})^T of Sec. 2 Step 1 as an explicit 0/1 matrix: row i has its
+    one 1 in the column of vertex i's aggregate."""
+    import scipy.sparse as sp
+    n = len(agg)
+    return sp.csr_matrix((np.ones(n), (np.arange(n), agg)), shape=(n, n_coarse))
+
+
+def _fiedler_space(L, rel=1e-6):
+    """Eigenvectors of L whose eigenvalue is lambda2 within `rel` (dense)."""
+    ev, V = np.linalg.eigh(L)
+    keep = [i for i in range(1, len(ev)) if ev[i] <= ev[1] * (1 + rel) + 1e-14]
+    return V[:, keep]
+
+
+def _subspace_cosine(x, Q):
+    x = x - x.mean()
+    x = x / np.linalg.norm(x)
+    Q, _ = np.linalg.qr(Q)
+    return float(np.linalg.norm(Q.T @ x))
+
+
+_CASCADE_GRAPHS = {
+    "grid_64x64_unit": lambda: inputs.grid2d(64, 64, "unit"),
+    "grid_14x9_unit": lambda: inputs.grid2d(14, 9, "unit"),
+    "grid_40x30_uniform": lambda: inputs.grid2d(40, 30, "uniform", seed=5),
+    "rgg_1500": lambda: inputs.rgg(1500, seed=3),
+    "path_300": lambda: inputs.path(300),
+}
+
+
+@pytest.mark.parametrize("name", ["grid_14x9_unit", "grid_40x30_uniform", "rgg_1500", "random_200"])
+def test_cascade_prolongs_with_the_explicit_transposed_restriction(name):
+    """Alg. 1 Step 3: the start of level j is (I_j^{j+1})^T applied to the
+    coarse result, with the restriction I_j^{j+1} of that same level j (Sec. 2
+    Step 1: (I)_pq = 1 iff q is in aggregate p), entry for entry; the coarsest
+    level starts from randn (Step 2).  Checked against an explicitly assembled
+    sparse matrix product on every level of each hierarchy."""
+    if name == "random_200":
+        rp, col, w = inputs.random_connected(200, 400, seed=103)
+    else:
+        rp, col, w = _CASCADE_GRAPHS[name]()
+    h = oracle.Hierarchy(rp, col, w, seed=21)
+    J = h.levels - 1
+    assert J >= 2
+    r = h.solve(trace=True)
+    sizes = h.sizes()
+    assert np.array_equal(r["start"][J], oracle.gaussian_start(21, sizes[J]))
+    for j in range(J):
+        P = _prolongation_matrix(h.agg(j), sizes[j + 1])
+        assert np.array_equal(r["start"][j], P @ r["end"][j + 1])
+        # each level's result is a unit vector orthogonal to 1 (Alg. 3)
+        assert abs(np.linalg.norm(r["end"][j]) - 1) <= 1e-14
+        assert abs(r["end"][j].sum()) <= 1e-13 * np.sqrt(sizes[j])
+    # the returned vector is level 0's result with the sign rule applied
+    assert np.array_equal(np.abs(r["u"]), np.abs(r["end"][0]))
+
+
+@pytest.mark.parametrize("name", sorted(_CASCADE_GRAPHS))
+def test_cascade_start_approximates_the_fiedler_vector(name):
+    """On graphs with geometric structure (grids, a random geometric graph, a
+    path) the coarse levels carry the Fiedler vector (Sec. 2, Step 3; Theorem
+    3.10 in the geometric setting): the prolonged start of every level j < J,
+    before any sweep, lies within a small angle of the exact Fiedler space of
+    L^j (dense eigensolver).  A random unit vector orthogonal to 1 has a cosine
+    of about 1/sqrt(n_j) <= 0.17 with it; a prolongation through a wrong map
+    or a discarded coarse result falls to that level."""
+    rp, col, w = _CASCADE_GRAPHS[name]()
+    h = oracle.Hierarchy(rp, col, w)
+    J = h.levels - 1
+    r = h.solve(trace=True)
+    for j in range(J):
+        Q = _fiedler_space(dense_laplacian(*h.csr(j)))
+        c = _subspace_cosine(r["start"][j], Q)
+        assert c >= 0.85, (j, c)
+
+
+@pytest.mark.parametrize("name", sorted(set(_CASCADE_GRAPHS) - {"grid_14x9_unit"}))
+def test_cascade_cuts_the_level0_sweeps(name):
+    """The point of Alg. 1 (Sec. 2, Table 3): level 0 starts close to the
+    Fiedler vector, so its power iteration stops after a small fraction of the
+    sweeps the same iteration needs from a Gaussian start at the same
+    tolerance (graphs of 300 to 4,096 vertices; the 126-vertex grid has too
+    few levels for a wide margin)."""
+    rp, col, w = _CASCADE_GRAPHS[name]()
+    n = len(rp) - 1
+    h = oracle.Hierarchy(rp, col, w)
+    k_cmg = int(h.solve()["sweeps"][0])
+    _, k_gauss, _, capped = oracle.power_iteration(rp, col, w, oracle.gaussian_start(7, n))
+    assert not capped
+    assert k_cmg <= 0.1 * k_gauss, (k_cmg, k_gauss)
+
+
+def test_resolve_from_a_given_start_vector():
+    """Re-solve on a kept hierarchy from a caller's start vector (the repeated
+    computations of the Remark after Alg. 1).  From the exact Fiedler vector
+    of a path (closed form) level 0 stops after one sweep on that vector;
+    from the coarsest level with Step 2's own Gaussian the result is the
+    ordinary solve; from a mid level the levels above are not visited."""
+    n = 300
+    rp, col, w = inputs.path(n)
+    h = oracle.Hierarchy(rp, col, w)
+    J = h.levels - 1
+    phi = np.cos(np.pi * (np.arange(n) + 0.5) / n)
+    phi /= np.linalg.norm(phi)
+    r = h.solve(start_level=0, x0=phi)
+    assert r["sweeps"][0] == 1 and (r["sweeps"][1:] == 0).all()
+    assert np.linalg.norm(align(r["u"], phi) - phi) <= 1e-13
+    assert r["lam"] == pytest.approx(2 - 2 * np.cos(np.pi / n), rel=1e-13)
+    base = h.solve(seed=5)
+    again = h.solve(start_level=J, x0=oracle.gaussian_start(5, h.sizes()[J]))
+    assert np.array_equal(base["u"], again["u"])
+    assert np.array_equal(base["sweeps"], again["sweeps"])
+    mid = h.solve(start_level=1, x0=oracle.gaussian_start(3, h.sizes()[1]), trace=True)
+    assert (mid["sweeps"][2:] == 0).all() and mid["sweeps"][1] >= 1
+    assert all(v is None for v in mid["start"][2:])
+    # a new seed moves the coarsest start, and with it the approximate vector
+    other = h.solve(seed=6)
+    assert not np.array_equal(base["u"], other["u"])
