@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "csr_from_edges", "grid2d", "grid3d", "path", "cycle", "complete", "star",
     "random_connected", "chung_lu", "rgg", "barabasi_albert", "largest_component",
-    "batch_graphs", "concat_csr", "serving_sizes", "serving_graphs",
+    "batch_graphs", "concat_csr", "serving_sizes", "serving_graphs", "hub_grid",
 ]
 
 
@@ -105,6 +105,23 @@ def grid3d(a: int, b: int, c: int, weights="uniform", seed=1412):
     u = np.concatenate([ex[0], ey[0], ez[0]])
     v = np.concatenate([ex[1], ey[1], ez[1]])
     return csr_from_edges(a * b * c, u, v, _weights(u.size, weights, rng))
+
+
+def hub_grid(a: int, b: int, hub_degree: int, seed=1412, hub_scale=1.0):
+    """An a x b 5-point grid (U[0.5, 1.5] weights) plus one extra vertex, id
+    a*b, joined to `hub_degree` distinct grid vertices drawn uniformly, with
+    weights hub_scale * U[0.5, 1.5]: the hub row of a power-law graph in a
+    graph small enough for exhaustive checks."""
+    rng = np.random.default_rng(seed)
+    rp, col, w = grid2d(a, b, "uniform", seed=seed + 1)
+    n = a * b
+    src = np.repeat(np.arange(n, dtype=np.int64), np.diff(rp))
+    keep = src < col
+    tgt = rng.choice(n, size=hub_degree, replace=False)
+    u = np.concatenate([src[keep], np.full(hub_degree, n, dtype=np.int64)])
+    v = np.concatenate([col[keep].astype(np.int64), tgt])
+    ww = np.concatenate([w[keep], hub_scale * rng.uniform(0.5, 1.5, size=hub_degree)])
+    return csr_from_edges(n + 1, u, v, ww)
 
 
 def path(n: int, w=None):

@@ -221,3 +221,34 @@ def test_stage_rule_picks_dense_power_law_levels():
     kind, staged = h.level_kernels()
     assert 2 not in kind and 1 in kind
     h.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_hub_row_split_into_many_chunks_matches_oracle(precision):
+    """A heavy row longer than 2,048 entries is cut into chunks that several
+    warps sum, and the warp of its last chunk waits for the others and adds
+    their partials in chunk order.  A hub of 12,000 entries (6 chunks) on a
+    22,501-vertex graph runs that path on level 0 (and its aggregate's row
+    on the next levels) at a size the oracle solves in seconds.  The hub's
+    weights are scaled by 1e-3 so that its degree does not set the shift
+    g far above the grid's degrees (which would stop every level after one
+    sweep)."""
+    rp, col, w = inputs.hub_grid(150, 150, 12000, seed=31, hub_scale=1e-3)
+    assert int(np.diff(rp).max()) == 12000
+    oh = oracle.Hierarchy(rp, col, w, seed=1412)
+    h = cmg.Hierarchy(rp, col, w, seed=1412, precision=precision)
+    kind, _ = h.level_kernels()
+    assert kind[0] in (1, 2)                 # level 0 runs the slice kernel
+    u, lam, st = h.fiedler()
+    u2, lam2, _ = h.fiedler()
+    assert np.array_equal(u, u2) and lam == lam2
+    h.close()
+    if precision == "fp64":
+        ref = oh.solve()
+        assert st["sweeps"] == ref["sweeps"].tolist()
+        assert aligned_err(u, ref["u"]) <= VEC_TOL
+        assert abs(lam - ref["lam"]) <= LAM_TOL * abs(ref["lam"])
+    else:
+        ref = oh.solve(schedule="replay", replay=st["sweeps"])
+        assert abs(lam - ref["lam"]) <= 1e-6 * abs(ref["lam"])
+        assert angle(u, ref["u"]) <= 1e-4
