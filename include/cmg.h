@@ -148,6 +148,42 @@ cmg_status_t cmg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, co
 cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double *lambda2_out,
                          cmg_stats_t *stats_out, void *stream);
 
+/* Options of one solve on a resident hierarchy (cmg_fiedler_ex). */
+typedef struct cmg_solve_options {
+    uint64_t seed;        /* keys the Gaussian start of Alg. 1 Step 2 for this solve
+                             (the hierarchy, whose visit orders the setup's seed keyed,
+                             is reused as it is)                                      */
+    const double *x0;     /* NULL: cascade from the coarsest level (Steps 2-3);
+                             else the start vector of level x0_level, double[n of that
+                             level] in that level's vertex order (level 0: the caller's
+                             order); levels above it are not visited                  */
+    int32_t x0_mem;       /* CMG_MEM_HOST or CMG_MEM_DEVICE (where x0 lives)           */
+    int32_t x0_level;     /* 0 .. levels-1                                             */
+    int32_t reserved[4];  /* must be 0                                                 */
+} cmg_solve_options_t;
+
+/* Fills *so for an ordinary solve of h: seed = the seed h was set up with
+ * (options.seed), no start vector.  h may be NULL (seed 1412).
+ * Errors: INVALID_ARG if so is NULL. */
+cmg_status_t cmg_solve_options_default(cmg_hierarchy_t h, cmg_solve_options_t *so);
+
+/*
+ * cmg_fiedler with per-solve options: a re-solve on a resident hierarchy with
+ * a new Gaussian start (another seed) or from a given start vector on any
+ * level, reusing the setup phase.  The Remark after Alg. 1 (Sec. 2) names
+ * applications that compute the Fiedler vector many times, such as recursive
+ * spectral bisection; there the setup is the part worth keeping.  With x0 on
+ * level s, Alg. 3 runs on level s from x0 (Gram-Schmidt against 1 first),
+ * then Step 3 continues from level s-1 down to 0 as usual; stats report 0
+ * sweeps for the levels above s.  A host x0 is copied before the solve
+ * starts (borrowed for the call only).  Other arguments, results and errors
+ * as cmg_fiedler; INVALID_ARG also for a bad x0_level / x0_mem or a nonzero
+ * reserved word.  Synchronises `stream`.
+ */
+cmg_status_t cmg_fiedler_ex(cmg_hierarchy_t h, const cmg_solve_options_t *so, double *u_out,
+                            int32_t u_mem, double *lambda2_out, cmg_stats_t *stats_out,
+                            void *stream);
+
 /* Level count and per-level sizes (host arrays of length >= levels, nullable). */
 cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_per_level,
                                 int64_t *nnz_per_level);
@@ -349,6 +385,14 @@ cmg_status_t cmg_server_add_graph(cmg_server_t s, int64_t n, const int64_t *row_
 /* Queues a solve of graph `graph_id`; u_out (host double[n], nullable) must
  * stay valid until the request completes.  *ticket identifies it. */
 cmg_status_t cmg_server_submit(cmg_server_t s, int64_t graph_id, double *u_out, int64_t *ticket);
+/* cmg_server_submit with per-solve options (cmg_fiedler_ex): a re-solve of a
+ * registered graph with another seed, or from a start vector x0 (host memory,
+ * borrowed until the request completes), on the graph's resident hierarchy
+ * when it has one.  Such a request never joins a batched job.
+ * Errors: INVALID_ARG for a NULL `so`, a device x0 or a nonzero reserved
+ * word; a bad x0_level is the request's own status. */
+cmg_status_t cmg_server_submit_ex(cmg_server_t s, int64_t graph_id, const cmg_solve_options_t *so,
+                                  double *u_out, int64_t *ticket);
 /* Blocks until the request completes; fills *out (nullable) and returns the
  * request's status.  A ticket can be waited for once. */
 cmg_status_t cmg_server_wait(cmg_server_t s, int64_t ticket, cmg_request_t *out);
@@ -417,9 +461,10 @@ cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int3
  *     are rejected with CMG_ERR_TOO_LARGE before any device work;
  *   - its scratch is one fixed array of about 8.4 MB in device memory that
  *     every GPU which loads this library holds until the process exits;
- *   - the first call on a device looks up that array's device address
- *     (cudaGetSymbolAddress) with the device current; make that first call
- *     before any stream capture;
+ *   - every call looks up that array's device address (cudaGetSymbolAddress,
+ *     which allocates nothing) with the device current; the first lookup on
+ *     a device loads the library's device code there, so make the first
+ *     call on each device before any stream capture;
  *   - all calls on a device share the array, so calls whose GPU work
  *     overlaps (other streams, other host threads) race and give wrong
  *     results: serialise them.  Each call clears what must start at zero.
@@ -437,6 +482,16 @@ cmg_status_t cmg_kernel_launches(uint64_t *count);
  * paper has no counterpart; it exists so out-of-memory handling can be
  * tested without exhausting the device. */
 cmg_status_t cmg_debug_fail_alloc_after(int64_t k);
+
+/* Test hook for the device-side timeout path: the `launch`-th next
+ * cooperative kernel launch of this library that uses more than one CTA
+ * (0: the next one, counted over all threads) never releases its grid
+ * barrier number `barrier` (0..254), so every CTA's bounded wait there runs
+ * out (after 20 ms instead of the usual 2 s), the kernel returns, and the
+ * call that issued it reports CMG_ERR_DEVICE_TIMEOUT; later launches of the
+ * same call return at their first barrier.  launch < 0 disarms.  The paper
+ * has no counterpart.  Errors: INVALID_ARG for a barrier outside 0..254. */
+cmg_status_t cmg_debug_stall_barrier(int64_t launch, int32_t barrier);
 
 #ifdef __cplusplus
 }

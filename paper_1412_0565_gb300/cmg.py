@@ -36,12 +36,13 @@ EXPORTS = [
     "cmg_hierarchy_info", "cmg_level_kernels", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
     "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
     "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
-    "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after",
+    "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after", "cmg_debug_stall_barrier",
     "cmg_setup_batch", "cmg_fiedler_batch", "cmg_batch_info", "cmg_batch_stats",
     "cmg_batch_get_aggregates", "cmg_batch_get_level_csr", "cmg_batch_set_replay",
     "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
     "cmg_batch_free", "cmg_server_config_default", "cmg_server_create", "cmg_server_add_graph",
-    "cmg_server_submit", "cmg_server_wait", "cmg_server_wait_for", "cmg_server_get_stats",
+    "cmg_server_submit", "cmg_server_submit_ex", "cmg_solve_options_default", "cmg_fiedler_ex",
+    "cmg_server_wait", "cmg_server_wait_for", "cmg_server_get_stats",
     "cmg_server_destroy",
 ]
 
@@ -82,6 +83,11 @@ class Stats(C.Structure):
                 "n": list(self.n[:L]), "nnz": list(self.nnz[:L]),
                 "sweeps": list(self.sweeps[:L]), "cos_final": list(self.cos_final[:L]),
                 "level_ms": list(self.level_ms[:L]), "finalize_ms": self.finalize_ms}
+
+
+class SolveOptions(C.Structure):
+    _fields_ = [("seed", C.c_uint64), ("x0", C.c_void_p), ("x0_mem", C.c_int32),
+                ("x0_level", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class BatchShape(C.Structure):
@@ -156,6 +162,7 @@ def load(build_if_stale: bool = True):
             "cmg_power_sweeps_noalloc": (I32, [I32, V, V, V, F64, V, I32, V, P(F64), V]),
             "cmg_kernel_launches": (I32, [P(C.c_uint64)]),
             "cmg_debug_fail_alloc_after": (I32, [I64]),
+            "cmg_debug_stall_barrier": (I32, [I64, I32]),
             "cmg_setup_batch": (I32, [I32, V, V, V, V, I32, P(Options), V, P(V)]),
             "cmg_fiedler_batch": (I32, [V, V, I32, V, V, V, V]),
             "cmg_batch_info": (I32, [V, P(I32), P(I32), I32, P(I64), P(I64)]),
@@ -172,6 +179,9 @@ def load(build_if_stale: bool = True):
             "cmg_server_create": (I32, [P(ServerConfig), P(Options), P(V)]),
             "cmg_server_add_graph": (I32, [V, I64, V, V, V, P(I64)]),
             "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
+            "cmg_server_submit_ex": (I32, [V, I64, P(SolveOptions), V, P(I64)]),
+            "cmg_solve_options_default": (I32, [V, P(SolveOptions)]),
+            "cmg_fiedler_ex": (I32, [V, P(SolveOptions), V, I32, P(F64), P(Stats), V]),
             "cmg_server_wait": (I32, [V, I64, P(Request)]),
             "cmg_server_wait_for": (I32, [V, I64, I64, P(Request)]),
             "cmg_server_get_stats": (I32, [V, P(ServerStats)]),
@@ -343,15 +353,33 @@ class Hierarchy:
                                         C.byref(g)), "level_csr")
         return rp, col, w, g.value
 
-    def fiedler(self, u_out=None, stream=None):
+    def fiedler(self, u_out=None, stream=None, *, seed=None, x0=None, x0_level=0):
         """Returns (u, lambda2, stats dict).  u_out: numpy (host) or torch CUDA
-        tensor (device) of n float64; allocated on the host when None."""
+        tensor (device) of n float64; allocated on the host when None.
+        seed / x0 / x0_level: a re-solve with another Gaussian start, or from
+        a start vector on level x0_level (cmg_fiedler_ex); x0 is numpy (host)
+        or a torch CUDA float64 tensor."""
         if u_out is None:
             u_out = np.empty(self.n, dtype=np.float64)
         p_u, mem = _ptr(u_out)
         lam = C.c_double()
         stats = Stats()
-        st = load().cmg_fiedler(self._h, p_u, mem, C.byref(lam), C.byref(stats), _stream(stream))
+        if seed is None and x0 is None:
+            st = load().cmg_fiedler(self._h, p_u, mem, C.byref(lam), C.byref(stats), _stream(stream))
+        else:
+            so = SolveOptions()
+            _check(load().cmg_solve_options_default(self._h, C.byref(so)), "solve_options")
+            if seed is not None:
+                so.seed = int(seed)
+            keep = None
+            if x0 is not None:
+                if isinstance(x0, np.ndarray):
+                    x0 = keep = np.ascontiguousarray(x0, dtype=np.float64)
+                p_x, xmem = _ptr(x0)
+                so.x0, so.x0_mem, so.x0_level = p_x, xmem, int(x0_level)
+            st = load().cmg_fiedler_ex(self._h, C.byref(so), p_u, mem, C.byref(lam), C.byref(stats),
+                                       _stream(stream))
+            del keep
         _check(st, "cmg_fiedler")
         return u_out, lam.value, stats.as_dict()
 
@@ -521,14 +549,29 @@ class Server:
         self._graphs.append((row_ptr, col, w))
         return gid.value
 
-    def submit(self, graph_id: int, want_vector: bool = True) -> int:
+    def submit(self, graph_id: int, want_vector: bool = True, *, seed=None, x0=None,
+               x0_level=0) -> int:
+        """Queues a solve; seed / x0 / x0_level make it a re-solve with its own
+        options (cmg_server_submit_ex; x0 is a host array, kept alive here
+        until the request is waited for)."""
         n = len(self._graphs[graph_id][0]) - 1
         u = np.empty(n, dtype=np.float64) if want_vector else None
         t = C.c_int64()
-        _check(load().cmg_server_submit(self._s, graph_id,
-                                        C.c_void_p(u.ctypes.data) if u is not None else None,
-                                        C.byref(t)), "server_submit", allow_warn=False)
-        self._outs[t.value] = u
+        pu = C.c_void_p(u.ctypes.data) if u is not None else None
+        keep = None
+        if seed is None and x0 is None:
+            _check(load().cmg_server_submit(self._s, graph_id, pu, C.byref(t)), "server_submit",
+                   allow_warn=False)
+        else:
+            so = SolveOptions()
+            _check(load().cmg_solve_options_default(None, C.byref(so)), "solve_options")
+            so.seed = int(self.opts.seed if seed is None else seed)
+            if x0 is not None:
+                keep = np.ascontiguousarray(x0, dtype=np.float64)
+                so.x0, so.x0_mem, so.x0_level = keep.ctypes.data, 0, int(x0_level)
+            _check(load().cmg_server_submit_ex(self._s, graph_id, C.byref(so), pu, C.byref(t)),
+                   "server_submit", allow_warn=False)
+        self._outs[t.value] = (u, keep)
         return t.value
 
     def wait(self, ticket: int, timeout_s: float | None = None):
@@ -541,7 +584,7 @@ class Server:
             st = load().cmg_server_wait_for(self._s, ticket, int(timeout_s * 1000), C.byref(r))
             if st == -12:
                 raise CmgError(st, "server_wait")
-        u = self._outs.pop(ticket, None)
+        u, _ = self._outs.pop(ticket, (None, None))
         _check(st, "server_wait")
         return u, r.as_dict()
 
@@ -634,3 +677,9 @@ def kernel_launches() -> int:
 
 def debug_fail_alloc_after(k: int):
     load().cmg_debug_fail_alloc_after(int(k))
+
+
+def debug_stall_barrier(launch: int, barrier: int = 0):
+    """Test hook: the launch-th next multi-CTA cooperative launch holds its grid
+    barrier number `barrier`, so its bounded waits run out (launch < 0: off)."""
+    _check(load().cmg_debug_stall_barrier(int(launch), int(barrier)), "debug_stall_barrier")

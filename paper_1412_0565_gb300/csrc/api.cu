@@ -471,20 +471,21 @@ cmg_status_t cmg_setup(int64_t n, const int64_t *row_ptr, const int32_t *col, co
 }
 
 
-cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double *lambda2_out,
-                         cmg_stats_t *stats_out, void *stream) {
-    if (!h) return CMG_ERR_INVALID_ARG;
-    if (u_out && u_mem != CMG_MEM_HOST && u_mem != CMG_MEM_DEVICE) return CMG_ERR_INVALID_ARG;
-    cudaStream_t s = (cudaStream_t)stream;
-    int prev = 0;
-    CMG_CUDA(cudaGetDevice(&prev));
-    if (prev != h->device) CMG_CUDA(cudaSetDevice(h->device));
+// Alg. 1 Steps 2-3 on a resident hierarchy.  seed keys the Gaussian start of
+// Step 2; x0 (device, nullable) replaces the cascade above level x0_level by
+// a given start vector on that level (levels above it are not visited).
+static cmg_status_t fiedler_impl(cmg_hierarchy_t h, uint64_t seed, const double *x0, int x0_level,
+                                 double *u_out, int32_t u_mem, double *lambda2_out,
+                                 cmg_stats_t *stats_out, cudaStream_t s) {
     const cmg_options_t &o = h->opts;
     const int J = (int)h->lv.size() - 1;
+    const int top = x0 ? x0_level : J;
     const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
     std::vector<PiLevel> views(J + 1);
     for (int j = 0; j <= J; j++) views[j] = level_view(h->lv[j]);
-    cmg_status_t st = CMG_OK;
+    // one error flag for every launch of this call (a timeout in any of them
+    // must reach the status)
+    cmg_status_t st = gs_clear(h->gs, s);
     const bool timing = o.timing != 0;
     std::vector<cudaEvent_t> ev;
     if (timing) {
@@ -492,12 +493,12 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
         for (auto &e : ev)
             if (cudaEventCreate(&e) != cudaSuccess) st = CMG_ERR_CUDA;
     }
-    for (int j = J; j >= 0 && st == CMG_OK; j--) {
+    for (int j = top; j >= 0 && st == CMG_OK; j--) {
         PiRun r = {};
         r.lv = &views[j];
         r.fp32 = fp32;
         r.tol = o.tol;
-        r.seed = o.seed;
+        r.seed = seed;
         r.max_sweeps = (j == J) ? o.max_sweeps_coarsest : o.max_sweeps;
         r.mode = 0;
         if (o.schedule == CMG_SCHEDULE_FIXED && j < J) {
@@ -507,7 +508,9 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
             r.mode = 1;
             r.k_fixed = o.replay_sweeps[j];
         }
-        if (j < J) {
+        if (j == top && x0) {
+            r.x_init = x0;
+        } else if (j < J) {
             for (int k = 0; k < 3; k++) r.coarse_bufs[k] = h->bufs[3 * (j + 1) + k];
             r.coarse_res = h->res + (j + 1);
             r.coarse_agg = h->lv[j].agg;
@@ -543,15 +546,17 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
     std::vector<double> level_ms(J + 2, 0.0);
     if (timing) {
         for (int j = 0; j <= J + 1 && st == CMG_OK; j++) {
+            if (j <= J && j > top) continue;
             float ms = 0.f;
             if (cudaEventElapsedTime(&ms, ev[2 * j], ev[2 * j + 1]) == cudaSuccess) level_ms[j] = ms;
         }
         for (auto &e : ev) cudaEventDestroy(e);
     }
-    if (prev != h->device) cudaSetDevice(prev);
     if (st != CMG_OK) return st;
+    // levels above the start level were not visited in this solve
+    for (int j = top + 1; j <= J; j++) hr[j] = PiResult{};
     int capped = 0;
-    for (int j = 0; j <= J; j++) capped |= hr[j].capped;
+    for (int j = 0; j <= top; j++) capped |= hr[j].capped;
     if (lambda2_out) *lambda2_out = out2[0];
     if (stats_out) {
         memset(stats_out, 0, sizeof(*stats_out));
@@ -569,6 +574,52 @@ cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double
         stats_out->finalize_ms = level_ms[J + 1];
     }
     return capped ? CMG_WARN_MAXITER : CMG_OK;
+}
+
+cmg_status_t cmg_fiedler(cmg_hierarchy_t h, double *u_out, int32_t u_mem, double *lambda2_out,
+                         cmg_stats_t *stats_out, void *stream) {
+    if (!h) return CMG_ERR_INVALID_ARG;
+    cmg_solve_options_t so;
+    cmg_solve_options_default(h, &so);
+    return cmg_fiedler_ex(h, &so, u_out, u_mem, lambda2_out, stats_out, stream);
+}
+
+cmg_status_t cmg_solve_options_default(cmg_hierarchy_t h, cmg_solve_options_t *so) {
+    if (!so) return CMG_ERR_INVALID_ARG;
+    memset(so, 0, sizeof(*so));
+    so->seed = h ? h->opts.seed : 1412;
+    so->x0_mem = CMG_MEM_HOST;
+    return CMG_OK;
+}
+
+cmg_status_t cmg_fiedler_ex(cmg_hierarchy_t h, const cmg_solve_options_t *so, double *u_out,
+                            int32_t u_mem, double *lambda2_out, cmg_stats_t *stats_out,
+                            void *stream) {
+    if (!h || !so) return CMG_ERR_INVALID_ARG;
+    if (u_out && u_mem != CMG_MEM_HOST && u_mem != CMG_MEM_DEVICE) return CMG_ERR_INVALID_ARG;
+    for (int k = 0; k < 4; k++)
+        if (so->reserved[k] != 0) return CMG_ERR_INVALID_ARG;
+    const int J = (int)h->lv.size() - 1;
+    if (so->x0 && (so->x0_level < 0 || so->x0_level > J ||
+                   (so->x0_mem != CMG_MEM_HOST && so->x0_mem != CMG_MEM_DEVICE)))
+        return CMG_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int prev = 0;
+    CMG_CUDA(cudaGetDevice(&prev));
+    if (prev != h->device) CMG_CUDA(cudaSetDevice(h->device));
+    const double *x0 = so->x0;
+    cmg_status_t st = CMG_OK;
+    if (x0 && so->x0_mem == CMG_MEM_HOST) {
+        // staged in the final-vector buffer (n_0 >= n of any level), which the
+        // solve writes only after the start level's power iteration has read it
+        const size_t nb = sizeof(double) * (size_t)h->lv[so->x0_level].n;
+        st = from_cuda(cudaMemcpyAsync(h->u_dev, x0, nb, cudaMemcpyHostToDevice, s));
+        x0 = h->u_dev;
+    }
+    if (st == CMG_OK)
+        st = fiedler_impl(h, so->seed, x0, so->x0_level, u_out, u_mem, lambda2_out, stats_out, s);
+    if (prev != h->device) cudaSetDevice(prev);
+    return st;
 }
 
 cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_per_level,
@@ -720,6 +771,7 @@ cmg_status_t cmg_power_sweeps(int32_t n, const int32_t *row_ptr, const int32_t *
     CMG_TRY(scr.get(&res, 1));
     CMG_TRY(scr.get(&gs, 1));
     CMG_TRY(scr.get(&out2, 2));
+    CMG_TRY(gs_clear(gs, s));
     PiRun r = {};
     r.lv = &lv;
     r.mode = 1;
@@ -760,6 +812,7 @@ cmg_status_t cmg_rayleigh_residual(int32_t n, const int32_t *row_ptr, const int3
     GridSync *gs;
     CMG_TRY(scr.get(&out2, 2));
     CMG_TRY(scr.get(&gs, 1));
+    CMG_TRY(gs_clear(gs, s));
     CMG_TRY(finalize(lv, 0, nullptr, nullptr, const_cast<double *>(u), 0, 1, out2, gs, s));
     double h2[2];
     GridSync hgs;
@@ -780,6 +833,12 @@ cmg_status_t cmg_kernel_launches(uint64_t *count) {
 
 cmg_status_t cmg_debug_fail_alloc_after(int64_t k) {
     debug_fail_alloc_after(k);
+    return CMG_OK;
+}
+
+cmg_status_t cmg_debug_stall_barrier(int64_t launch, int32_t barrier) {
+    if (launch >= 0 && (barrier < 0 || barrier > 254)) return CMG_ERR_INVALID_ARG;
+    debug_stall_barrier(launch, barrier);
     return CMG_OK;
 }
 

@@ -81,12 +81,17 @@ cmg_status_t device_info(DeviceInfo *out);
 
 // ----------------------------------------------------------------- grid barrier
 // State of one cooperative launch.  `count` and `gen` implement a sense-free
-// generation barrier; `err` records a barrier wait that ran out of time.
+// generation barrier and are cleared before every launch; `err` records a
+// barrier wait that ran out of time and is cleared once per API call, so a
+// timeout in any launch of a call reaches the host (every later launch of
+// the call returns at its first barrier).  `stall` is a test hook: when its
+// low byte is b > 0, barrier number b - 1 of the launch is never released,
+// so its waits run out (after kStallTimeoutNs); 0 in normal operation.
 struct GridSync {
     unsigned int count;
     unsigned int gen;
+    unsigned int stall;
     unsigned int err;
-    unsigned int pad;
 };
 
 // Nanoseconds since an arbitrary origin (device global timer).
@@ -98,6 +103,8 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // A barrier wait gives up after this long and sets GridSync::err.
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;
+// The same for a launch with the stall hook armed (keeps its test short).
+constexpr unsigned long long kStallTimeoutNs = 20000000ull;
 
 __device__ __forceinline__ unsigned int ld_acquire_gpu(const unsigned int *p) {
     unsigned int v;
@@ -130,17 +137,22 @@ __device__ __forceinline__ void red_add_release_gpu(unsigned int *p, unsigned in
 // counter (releasing the CTA's writes, ordered before it by __syncthreads);
 // the last arriver resets the counter and releases a generation number that
 // the others poll with acquire loads.  A wait gives up after
-// kBarrierTimeoutNs and sets GridSync::err.  Returns false (in every thread
-// of the CTA) when this or an earlier barrier timed out; callers then return.
+// kBarrierTimeoutNs and sets GridSync::err; a wait also ends as soon as err
+// is seen set.  Returns false (in every thread of the CTA) when this or an
+// earlier barrier of the call timed out; callers then return.
 __device__ __forceinline__ bool grid_sync(GridSync *gs) {
     __shared__ int s_ok;
     __syncthreads();
     if (gridDim.x == 1) return true;
     if (threadIdx.x == 0) {
+        // the hook word is read beside the arrival, off its critical path
+        const unsigned int stall = ld_relaxed_gpu(&gs->stall) & 0xffu;
         const unsigned int g0 = ld_relaxed_gpu(&gs->gen);
         const unsigned int arrived = atom_add_acq_rel_gpu(&gs->count, 1u);
+        const bool held = stall != 0u && stall == g0 + 1u;
+        const unsigned long long limit = stall ? kStallTimeoutNs : kBarrierTimeoutNs;
         int ok = 1;
-        if (arrived == gridDim.x - 1) {
+        if (arrived == gridDim.x - 1 && !held) {
             st_relaxed_gpu(&gs->count, 0u);
             red_add_release_gpu(&gs->gen, 1u);
         } else {
@@ -151,7 +163,7 @@ __device__ __forceinline__ bool grid_sync(GridSync *gs) {
                     const unsigned long long t = global_ns();
                     if (t0 == 0) {
                         t0 = t;
-                    } else if (t - t0 > kBarrierTimeoutNs) {
+                    } else if (t - t0 > limit) {
                         atomicExch(&gs->err, 1u);
                         ok = 0;
                         break;
@@ -234,8 +246,15 @@ cmg_status_t allow_max_dynamic_smem(const void *kernel);
 // Largest co-resident grid for a cooperative launch of `kernel`.
 cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *out);
 
-// Launches `kernel` cooperatively with a zeroed GridSync at `gs`.
+// Launches `kernel` cooperatively after clearing the barrier counters of
+// `gs` (count, gen; the stall hook is set when armed); `err` is kept, so
+// clear it with gs_clear once at the start of each API call.
 cmg_status_t coop_launch(const void *kernel, int blocks, int threads, size_t smem,
                          cudaStream_t s, void **args, GridSync *gs);
+// Clears all of `gs` (stream-ordered).
+cmg_status_t gs_clear(GridSync *gs, cudaStream_t s);
+// Test hook: the `launch`-th next cooperative launch with more than one CTA
+// (0: the next) holds its barrier number `barrier`; launch < 0 disarms.
+void debug_stall_barrier(long long launch, int barrier);
 
 }  // namespace cmg

@@ -418,6 +418,7 @@ cmg_status_t hec_level(int n, long long nnz, const int *rp, const int *col, cons
     GridSync *gs;
     CMG_TRY(scr.get(&c_dev, 1));
     CMG_TRY(scr.get(&gs, 1));
+    CMG_TRY(gs_clear(gs, s));
     CMG_TRY(hec_level_async(n, nnz, rp, col, w, seed, level, rank, agg_out, c_dev, gs, s));
     int c = 0;
     GridSync hgs;

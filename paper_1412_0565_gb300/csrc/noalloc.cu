@@ -3,13 +3,11 @@
 //
 // Its scratch (three iterate vectors, g - d_i, row tiles, partial sums, the result
 // record, barrier state and the shift) lives in one file-scope __device__
-// array.  Host code must not use the array's name as a device address: on
-// first use on a device, with that device current, the address is looked up
-// with cudaGetSymbolAddress and cached per device.  Every call on a device
+// array.  Host code must not use the array's name as a device address: each
+// call looks the address up with cudaGetSymbolAddress on the current device
+// (the first lookup on a device loads the module there).  Every call on a device
 // shares the array, so calls whose work overlaps on the GPU race; everything
 // that must start from zero is cleared by the call itself.
-#include <mutex>
-
 #include "internal.h"
 
 namespace {
@@ -36,23 +34,14 @@ constexpr size_t kBytes = kOffG + align256(sizeof(double));
 // The scratch of every cmg_power_sweeps_noalloc call on this device.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kBytes];
 
-std::mutex g_mu;
-void *g_base[64] = {};
-
-// Device address of the scratch array for the current device (looked up once).
+// Device address of the scratch array on the current device.  Looked up on
+// every call (cudaGetSymbolAddress allocates nothing): a cached address
+// would go stale if the context were destroyed and the module loaded again.
 cmg_status_t scratch_base(unsigned char **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cmg::from_cuda(e);
-    if (dev < 0 || dev >= 64) return CMG_ERR_CUDA;
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_base[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cmg::from_cuda(e != cudaSuccess ? e : cudaErrorUnknown);
-        g_base[dev] = p;
-    }
-    *out = static_cast<unsigned char *>(g_base[dev]);
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cmg::from_cuda(e != cudaSuccess ? e : cudaErrorUnknown);
+    *out = static_cast<unsigned char *>(p);
     return CMG_OK;
 }
 
@@ -81,6 +70,7 @@ extern "C" cmg_status_t cmg_power_sweeps_noalloc(int32_t n, const int32_t *row_p
     GridSync *gs = reinterpret_cast<GridSync *>(base + kOffSync);
     double *out2 = reinterpret_cast<double *>(base + kOffOut);
     double *gdev = reinterpret_cast<double *>(base + kOffG);
+    CMG_TRY(gs_clear(gs, s));
     if (!(g > 0.0)) {
         CMG_TRY(launch_gershgorin(n, row_ptr, w, gdev, s));
         CMG_CUDA(cudaMemcpyAsync(&g, gdev, sizeof(double), cudaMemcpyDeviceToHost, s));

@@ -1,5 +1,6 @@
 // runtime.cu -- error mapping, the library's device memory pool, device
 // properties and cooperative-launch helpers.
+#include <stddef.h>
 #include <stdio.h>
 #include <stdlib.h>
 
@@ -153,9 +154,45 @@ cmg_status_t coop_max_blocks(const void *kernel, int threads, size_t smem, int *
     return CMG_OK;
 }
 
+namespace {
+// stall hook: multi-CTA cooperative launches still to pass before the held
+// one (-1: off), and the barrier it holds
+std::atomic<long long> g_stall_launch{-1};
+std::atomic<int> g_stall_barrier{0};
+}  // namespace
+
+void debug_stall_barrier(long long launch, int barrier) {
+    g_stall_barrier.store(barrier);
+    g_stall_launch.store(launch);
+}
+
+cmg_status_t gs_clear(GridSync *gs, cudaStream_t s) {
+    CMG_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), s));
+    return CMG_OK;
+}
+
 cmg_status_t coop_launch(const void *kernel, int blocks, int threads, size_t smem,
                          cudaStream_t s, void **args, GridSync *gs) {
-    CMG_CUDA(cudaMemsetAsync(gs, 0, sizeof(GridSync), s));
+    // count, gen and stall lie before err, which this leaves alone
+    static_assert(offsetof(GridSync, err) == 3 * sizeof(unsigned int), "GridSync layout");
+    int hold = 0;
+    if (blocks > 1) {
+        long long k = g_stall_launch.load();
+        while (k >= 0 && !g_stall_launch.compare_exchange_weak(k, k - 1)) {
+        }
+        if (k == 0) {
+            const int b = g_stall_barrier.load();
+            hold = 1 + (b < 0 ? 0 : (b > 254 ? 254 : b));
+        }
+    }
+    if (hold == 0) {
+        CMG_CUDA(cudaMemsetAsync(gs, 0, 3 * sizeof(unsigned int), s));
+    } else {
+        CMG_CUDA(cudaMemsetAsync(gs, 0, 2 * sizeof(unsigned int), s));
+        // every byte of the stall word is 1 + the barrier index; the barrier
+        // reads the low one
+        CMG_CUDA(cudaMemsetAsync(&gs->stall, hold, sizeof(unsigned int), s));
+    }
     CMG_CUDA(cudaLaunchCooperativeKernel(kernel, dim3(blocks), dim3(threads), args, smem, s));
     return launch_status();
 }

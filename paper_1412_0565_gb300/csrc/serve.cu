@@ -57,6 +57,8 @@ struct Request {
     int64_t ticket = 0;
     int64_t gid = 0;
     double *u_out = nullptr;
+    bool custom = false;           // solved with its own options (never batched)
+    cmg_solve_options_t so;
     cmg_request_t res;
     bool done = false;
 };
@@ -131,13 +133,13 @@ Job pick_job(cmg_server_s *S) {
             return job;
         }
         const size_t est = estimate(S, g);
-        bool small = g.n <= S->cfg.batch_max_n && S->cfg.max_batch > 1;
+        bool small = g.n <= S->cfg.batch_max_n && S->cfg.max_batch > 1 && !r->custom;
         if (small) {
             // batch only when enough small cold requests wait for it
             int waiting = 0;
             for (auto jt = it; jt != S->pending.end() && waiting < S->cfg.min_batch; ++jt) {
                 const Graph &gj = S->graphs[(*jt)->gid];
-                if (!gj.busy && !gj.h && gj.n <= S->cfg.batch_max_n) waiting++;
+                if (!gj.busy && !gj.h && gj.n <= S->cfg.batch_max_n && !(*jt)->custom) waiting++;
             }
             small = waiting >= S->cfg.min_batch;
         }
@@ -167,7 +169,7 @@ Job pick_job(cmg_server_s *S) {
         size_t total = 0;
         for (auto jt = it; jt != S->pending.end() && (int)take.size() < S->cfg.max_batch; ++jt) {
             Graph &gj = S->graphs[(*jt)->gid];
-            if (gj.busy || gj.h || gj.n > S->cfg.batch_max_n) continue;
+            if (gj.busy || gj.h || gj.n > S->cfg.batch_max_n || (*jt)->custom) continue;
             const size_t e = estimate(S, gj);
             if (!make_room(S, total + e)) break;
             total += e;
@@ -214,7 +216,9 @@ void run_job(cmg_server_s *S, Job &job, cudaStream_t s) {
         if (job.kind == 1) st = cmg_setup(g.n, g.rp, g.col, g.w, CMG_MEM_HOST, &S->opts, s, &h);
         cmg_stats_t stt;
         double lam = 0.0;
-        if (st == CMG_OK) st = cmg_fiedler(h, r->u_out, CMG_MEM_HOST, &lam, &stt, s);
+        if (st == CMG_OK)
+            st = r->custom ? cmg_fiedler_ex(h, &r->so, r->u_out, CMG_MEM_HOST, &lam, &stt, s)
+                           : cmg_fiedler(h, r->u_out, CMG_MEM_HOST, &lam, &stt, s);
         r->res.status = st;
         r->res.lambda2 = lam;
         r->res.residual = (st == CMG_OK || st == CMG_WARN_MAXITER) ? stt.residual : 0.0;
@@ -404,9 +408,14 @@ extern "C" cmg_status_t cmg_server_add_graph(cmg_server_t S, int64_t n, const in
     return CMG_OK;
 }
 
-extern "C" cmg_status_t cmg_server_submit(cmg_server_t S, int64_t graph_id, double *u_out,
-                                          int64_t *ticket) {
+static cmg_status_t submit_impl(cmg_server_t S, int64_t graph_id, const cmg_solve_options_t *so,
+                                double *u_out, int64_t *ticket) {
     if (!S || !ticket) return CMG_ERR_INVALID_ARG;
+    if (so) {
+        for (int k = 0; k < 4; k++)
+            if (so->reserved[k] != 0) return CMG_ERR_INVALID_ARG;
+        if (so->x0 && (so->x0_mem != CMG_MEM_HOST || so->x0_level < 0)) return CMG_ERR_INVALID_ARG;
+    }
     Request *r = new Request();
     {
         std::lock_guard<std::mutex> lk(S->mu);
@@ -417,6 +426,10 @@ extern "C" cmg_status_t cmg_server_submit(cmg_server_t S, int64_t graph_id, doub
         r->ticket = S->next_ticket++;
         r->gid = graph_id;
         r->u_out = u_out;
+        if (so) {
+            r->custom = true;
+            r->so = *so;
+        }
         memset(&r->res, 0, sizeof(r->res));
         r->res.submit_ns = now_ns();
         S->reqs[r->ticket] = r;
@@ -425,6 +438,18 @@ extern "C" cmg_status_t cmg_server_submit(cmg_server_t S, int64_t graph_id, doub
     }
     S->cv_work.notify_one();
     return CMG_OK;
+}
+
+extern "C" cmg_status_t cmg_server_submit(cmg_server_t S, int64_t graph_id, double *u_out,
+                                          int64_t *ticket) {
+    return submit_impl(S, graph_id, nullptr, u_out, ticket);
+}
+
+extern "C" cmg_status_t cmg_server_submit_ex(cmg_server_t S, int64_t graph_id,
+                                             const cmg_solve_options_t *so, double *u_out,
+                                             int64_t *ticket) {
+    if (!so) return CMG_ERR_INVALID_ARG;
+    return submit_impl(S, graph_id, so, u_out, ticket);
 }
 
 static cmg_status_t wait_impl(cmg_server_t S, int64_t ticket, int64_t timeout_ms, cmg_request_t *out) {

@@ -106,3 +106,64 @@ def test_injected_allocation_failures_are_reported_and_recoverable():
     assert "OOM" in seen
     u, lam, _ = cmg.fiedler(rp, col, w)
     assert np.array_equal(u, ok_u) and lam == ok_lam
+
+
+# ------------------------------------------------------------------ device-side waits that run out
+# The stall hook makes one grid barrier of one launch never release, so every
+# CTA's bounded wait there runs out (20 ms), the kernel returns, and the call
+# must report ERR_DEVICE_TIMEOUT even though later launches of the same call
+# (the next levels, the final pass) run after it.  No fault is involved: the
+# waits are the library's own bounded spins, and the context stays usable.
+def _stalled(fn, launch=0, barrier=1):
+    cmg.debug_stall_barrier(launch, barrier)
+    try:
+        fn()
+    except cmg.CmgError as e:
+        return e.name
+    finally:
+        cmg.debug_stall_barrier(-1, 0)
+    return "OK"
+
+
+def test_timeout_in_a_non_final_launch_reaches_cmg_fiedler():
+    rp, col, w = inputs.grid2d(200, 200, "uniform", seed=4)
+    with cmg.Hierarchy(rp, col, w) as h:
+        kinds, _ = h.level_kernels()
+        assert kinds[0] in (1, 2)            # level 0 runs the multi-CTA slice kernel
+        ok_u, ok_lam, _ = h.fiedler()
+        # the first multi-CTA launch of the solve is a power-iteration launch;
+        # the final-vector launch (and maybe more levels) follow it
+        assert _stalled(h.fiedler) == "ERR_DEVICE_TIMEOUT"
+        u, lam, _ = h.fiedler()
+        assert np.array_equal(u, ok_u) and lam == ok_lam
+
+
+def test_timeout_in_setup_is_reported():
+    rp, col, w = inputs.grid2d(200, 200, "uniform", seed=4)
+    ok_u, ok_lam, _ = cmg.fiedler(rp, col, w)
+    # the coarsening kernel of level 0 is the first multi-CTA launch of setup
+    assert _stalled(lambda: cmg.Hierarchy(rp, col, w).close(), barrier=0) == "ERR_DEVICE_TIMEOUT"
+    u, lam, _ = cmg.fiedler(rp, col, w)
+    assert np.array_equal(u, ok_u) and lam == ok_lam
+
+
+@pytest.mark.parametrize("entry", ["power_sweeps", "power_sweeps_noalloc"])
+def test_timeout_in_the_sweep_launch_reaches_the_step_entry_points(entry):
+    rp, col, w = inputs.grid2d(200, 200, "uniform", seed=4)
+    dev = torch.device("cuda")
+    rp32 = torch.tensor(rp.astype(np.int32), device=dev)
+    c = torch.tensor(col, device=dev)
+    wt = torch.tensor(w, device=dev)
+    x = torch.tensor(np.random.default_rng(3).standard_normal(len(rp) - 1), device=dev)
+    fn = getattr(cmg, entry)
+    u0, cos0 = fn(rp32, c, wt, x, 40)
+    # the sweep launch is followed by the final-vector launch in the same call
+    assert _stalled(lambda: fn(rp32, c, wt, x, 40)) == "ERR_DEVICE_TIMEOUT"
+    u1, cos1 = fn(rp32, c, wt, x, 40)
+    assert torch.equal(u0, u1) and cos0 == cos1
+
+
+def test_stall_hook_rejects_a_bad_barrier_index():
+    with pytest.raises(cmg.CmgError):
+        cmg.debug_stall_barrier(0, 255)
+    cmg.debug_stall_barrier(-1, 0)
