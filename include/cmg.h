@@ -62,6 +62,15 @@ typedef enum cmg_status {
 } cmg_status_t;
 
 enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 };
+/* Sweep precision.  FP64: every power-iteration sweep in FP64.  FP32_SWEEP:
+ * the sweeps of the levels that carry the bytes run in FP32 with FP32
+ * accumulation -- in cmg_setup / cmg_fiedler the levels of more than 65,536
+ * rows, in the batched form union level 0 -- and every other level keeps
+ * FP64 sweeps (those levels are latency-bound and run the longest sweep
+ * chains, along which FP32 rounding would accumulate); in both forms the
+ * stop statistic, mean and norm are float-float sums (about 48 bits), and
+ * the last level-0 sweep is recomputed in FP64 from the previous iterate.
+ * cmg_level_precision reports each level's choice. */
 enum { CMG_PRECISION_FP64 = 0, CMG_PRECISION_FP32_SWEEP = 1 };
 enum { CMG_SCHEDULE_TOL = 0, CMG_SCHEDULE_FIXED = 1, CMG_SCHEDULE_REPLAY = 2 };
 
@@ -198,6 +207,11 @@ cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_p
  * level), read by cmg_setup, overrides that.  Results do not depend on the
  * kernel.  Errors: INVALID_ARG if h is NULL. */
 cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *staged_out);
+
+/* Sweep precision of each level (host int32 array of length >= levels):
+ * CMG_PRECISION_FP32_SWEEP or CMG_PRECISION_FP64 (see the precision enum).
+ * Errors: INVALID_ARG if h or prec_out is NULL. */
+cmg_status_t cmg_level_precision(cmg_hierarchy_t h, int32_t *prec_out);
 
 /* Device bytes held by the hierarchy (levels and solve workspace). */
 cmg_status_t cmg_hierarchy_device_bytes(cmg_hierarchy_t h, size_t *bytes);

@@ -33,7 +33,7 @@ STATUS = {
 # every symbol include/cmg.h declares
 EXPORTS = [
     "cmg_options_default", "cmg_status_string", "cmg_version", "cmg_setup", "cmg_fiedler",
-    "cmg_hierarchy_info", "cmg_level_kernels", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
+    "cmg_hierarchy_info", "cmg_level_kernels", "cmg_level_precision", "cmg_hierarchy_device_bytes", "cmg_estimate_device_bytes",
     "cmg_get_aggregates", "cmg_get_level_csr", "cmg_free", "cmg_heaviest_neighbour",
     "cmg_visit_ranks", "cmg_hec_aggregate", "cmg_power_sweeps", "cmg_rayleigh_residual",
     "cmg_power_sweeps_noalloc", "cmg_kernel_launches", "cmg_debug_fail_alloc_after", "cmg_debug_stall_barrier",
@@ -179,6 +179,7 @@ def load(build_if_stale: bool = True):
             "cmg_server_create": (I32, [P(ServerConfig), P(Options), P(V)]),
             "cmg_server_add_graph": (I32, [V, I64, V, V, V, P(I64)]),
             "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
+            "cmg_level_precision": (I32, [V, V]),
             "cmg_server_submit_ex": (I32, [V, I64, P(SolveOptions), V, P(I64)]),
             "cmg_solve_options_default": (I32, [V, P(SolveOptions)]),
             "cmg_fiedler_ex": (I32, [V, P(SolveOptions), V, I32, P(F64), P(Stats), V]),
@@ -330,6 +331,12 @@ class Hierarchy:
         _check(load().cmg_level_kernels(self._h, C.c_void_p(kind.ctypes.data),
                                         C.c_void_p(staged.ctypes.data)), "level_kernels")
         return kind.tolist(), staged.tolist()
+
+    def level_precision(self):
+        """Per level: "fp32" or "fp64" sweeps."""
+        p = np.zeros(self.levels, dtype=np.int32)
+        _check(load().cmg_level_precision(self._h, C.c_void_p(p.ctypes.data)), "level_precision")
+        return ["fp32" if x == 1 else "fp64" for x in p.tolist()]
 
     def device_bytes(self) -> int:
         b = C.c_size_t()

@@ -93,6 +93,7 @@ struct LevelData {
     double g = 0.0;
     bool has_lay = false;   // large level: sweeps read the sweep layout
     SweepLayout lay;
+    int fp32 = 0;           // this level's sweeps run in FP32
 };
 
 struct cmg_hierarchy_s {
@@ -218,6 +219,9 @@ cmg_status_t cmg::launch_to_float(long long m, const double *w, float *w32, cuda
     return launch_status();
 }
 
+// Fewest rows of a level that sweeps in FP32 in the FP32 form.
+constexpr int kFp32MinRows = 65536;
+
 static PiLevel level_view(const LevelData &L) {
     PiLevel v;
     v.n = L.n;
@@ -320,52 +324,62 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         if (st != CMG_OK) return st;
         level++;
     }
-    // ---- FP32 copies of the weights for the FP32 sweep form
-    if (o.precision == CMG_PRECISION_FP32_SWEEP) {
-        for (auto &L : h->lv) {
-            CMG_TRY(dev_alloc_n(&L.w32, (size_t)std::max<long long>(L.nnz, 1), s));
-            CMG_TRY(launch_to_float(L.nnz, L.w, L.w32, s));
+    // ---- sweep precision per level.  In the FP32 form only levels of more
+    // than kFp32MinRows rows sweep in FP32: those carry the bytes that FP32
+    // halves.  Smaller levels keep FP64 sweeps: their sweeps are latency-bound
+    // (FP32 saves little there), and they run the longest sweep chains
+    // (thousands of sweeps on the coarse levels), along which FP32 rounding
+    // accumulates in slowly converging components that the finer levels
+    // inherit (measured: up to 3e-6 relative in lambda2 on preferential-
+    // attachment graphs whose coarse levels ran in FP32).
+    const int form32 = o.precision == CMG_PRECISION_FP32_SWEEP;
+    const int nlev = (int)h->lv.size();
+    {
+        unsigned long long *cnt;
+        CMG_TRY(scr.get(&cnt, 1));
+        for (int k = 0; k < nlev; k++) {
+            LevelData &L = h->lv[k];
+            if (k == 0 && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
+            L.fp32 = (form32 && L.n > kFp32MinRows) ? 1 : 0;
         }
     }
-    // ---- SELL-32 sizes (small levels); sweep layouts for the levels the
-    // shared-memory kernel cannot hold
+    for (auto &L : h->lv) {
+        if (!L.fp32) continue;
+        CMG_TRY(dev_alloc_n(&L.w32, (size_t)std::max<long long>(L.nnz, 1), s));
+        CMG_TRY(launch_to_float(L.nnz, L.w, L.w32, s));
+    }
+    // ---- sweep layouts for the levels the shared-memory kernel cannot hold
     size_t lay_bytes = 0;
-    const int nlev = (int)h->lv.size();
     std::vector<int> stage_try(nlev, 0);
     std::vector<unsigned long long> below(nlev, 0);
     unsigned long long *below_dev = nullptr;
     {
-        unsigned long long *cnt;
         int *voff1;
-        CMG_TRY(scr.get(&cnt, 1));
         CMG_TRY(scr.get(&voff1, 2));
         CMG_TRY(scr.get(&below_dev, (size_t)nlev));
-        const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
-        const int cap = stage_capacity(fp32);
         for (int k = 0; k < nlev; k++) {
             LevelData &L = h->lv[k];
-            if (k == 0 && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
-            if (small_level_fits(level_view(L), fp32)) continue;
+            if (small_level_fits(level_view(L), L.fp32)) continue;
             const int hv[2] = {0, L.n};
             CMG_CUDA(cudaMemcpyAsync(voff1, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
-            CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, fp32,
+            CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, L.fp32,
                                        &L.lay, &lay_bytes, s));
             L.has_lay = true;
             // gathers that a staged prefix of the iterate would serve
-            stage_try[k] = std::min(L.n, cap);
+            stage_try[k] = std::min(L.n, stage_capacity(L.fp32));
             if (stage_try[k] > 0) CMG_TRY(layout_count_below(L.lay, stage_try[k], below_dev + k, s));
         }
     }
-    // ---- solve workspace: a buffer pair per level, results, barrier state
-    const size_t esz = (o.precision == CMG_PRECISION_FP32_SWEEP) ? sizeof(float) : sizeof(double);
+    // ---- solve workspace: an iterate ring per level, results, barrier state
     for (auto &L : h->lv) {
+        const size_t esz = L.fp32 ? sizeof(float) : sizeof(double);
         for (int k = 0; k < 3; k++) {
             void *p = nullptr;
             CMG_TRY(dev_alloc(&p, esz * (size_t)L.n, s));
             h->bufs.push_back(p);
         }
         double *gdp = nullptr;
-        if (o.precision == CMG_PRECISION_FP64) CMG_TRY(dev_alloc_n(&gdp, (size_t)L.n, s));
+        if (!L.fp32) CMG_TRY(dev_alloc_n(&gdp, (size_t)L.n, s));
         h->gd.push_back(gdp);
     }
     CMG_TRY(dev_alloc_n(&h->res, h->lv.size(), s));
@@ -378,8 +392,8 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         bytes += sizeof(int) * ((size_t)L.n + 1) + (sizeof(int) + sizeof(double)) * (size_t)L.nnz;
         if (L.w32) bytes += sizeof(float) * (size_t)L.nnz;
         if (L.agg) bytes += sizeof(int) * (size_t)L.n;
-        bytes += 3 * esz * (size_t)L.n;
-        if (o.precision == CMG_PRECISION_FP64) bytes += sizeof(double) * (size_t)L.n;
+        bytes += 3 * (L.fp32 ? sizeof(float) : sizeof(double)) * (size_t)L.n;
+        if (!L.fp32) bytes += sizeof(double) * (size_t)L.n;
     }
     bytes += sizeof(double) * (size_t)n;
     h->bytes = bytes + lay_bytes;
@@ -480,7 +494,6 @@ static cmg_status_t fiedler_impl(cmg_hierarchy_t h, uint64_t seed, const double 
     const cmg_options_t &o = h->opts;
     const int J = (int)h->lv.size() - 1;
     const int top = x0 ? x0_level : J;
-    const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
     std::vector<PiLevel> views(J + 1);
     for (int j = 0; j <= J; j++) views[j] = level_view(h->lv[j]);
     // one error flag for every launch of this call (a timeout in any of them
@@ -496,7 +509,7 @@ static cmg_status_t fiedler_impl(cmg_hierarchy_t h, uint64_t seed, const double 
     for (int j = top; j >= 0 && st == CMG_OK; j--) {
         PiRun r = {};
         r.lv = &views[j];
-        r.fp32 = fp32;
+        r.fp32 = h->lv[j].fp32;
         r.tol = o.tol;
         r.seed = seed;
         r.max_sweeps = (j == J) ? o.max_sweeps_coarsest : o.max_sweeps;
@@ -512,6 +525,7 @@ static cmg_status_t fiedler_impl(cmg_hierarchy_t h, uint64_t seed, const double 
             r.x_init = x0;
         } else if (j < J) {
             for (int k = 0; k < 3; k++) r.coarse_bufs[k] = h->bufs[3 * (j + 1) + k];
+            r.coarse_fp64 = h->lv[j + 1].fp32 ? 0 : 1;
             r.coarse_res = h->res + (j + 1);
             r.coarse_agg = h->lv[j].agg;
             r.coarse_inv = h->lv[j + 1].has_lay ? h->lv[j + 1].lay.inv : nullptr;
@@ -526,7 +540,7 @@ static cmg_status_t fiedler_impl(cmg_hierarchy_t h, uint64_t seed, const double 
     double *u_dev = (u_out && u_mem == CMG_MEM_DEVICE) ? u_out : h->u_dev;
     if (timing && st == CMG_OK) cudaEventRecord(ev[2 * (J + 1)], s);
     if (st == CMG_OK)
-        st = finalize(views[0], fp32, &h->bufs[0], h->res, u_dev, 1, 0, h->out2, h->gs, s);
+        st = finalize(views[0], h->lv[0].fp32, &h->bufs[0], h->res, u_dev, 1, 0, h->out2, h->gs, s);
     if (timing && st == CMG_OK) cudaEventRecord(ev[2 * (J + 1) + 1], s);
     std::vector<PiResult> hr(J + 1);
     double out2[2] = {0.0, 0.0};
@@ -635,16 +649,22 @@ cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_p
 
 cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *staged_out) {
     if (!h) return CMG_ERR_INVALID_ARG;
-    const int fp32 = h->opts.precision == CMG_PRECISION_FP32_SWEEP;
     for (size_t j = 0; j < h->lv.size(); j++) {
         const LevelData &L = h->lv[j];
         const int staged = L.has_lay ? L.lay.stage_n : 0;
         int kind = 0;
         if (L.has_lay) kind = staged > 0 ? 2 : 1;
-        else if (!small_level_fits(level_view(L), fp32)) kind = 3;
+        else if (!small_level_fits(level_view(L), L.fp32)) kind = 3;
         if (kind_out) kind_out[j] = kind;
         if (staged_out) staged_out[j] = staged;
     }
+    return CMG_OK;
+}
+
+cmg_status_t cmg_level_precision(cmg_hierarchy_t h, int32_t *prec_out) {
+    if (!h || !prec_out) return CMG_ERR_INVALID_ARG;
+    for (size_t j = 0; j < h->lv.size(); j++)
+        prec_out[j] = h->lv[j].fp32 ? CMG_PRECISION_FP32_SWEEP : CMG_PRECISION_FP64;
     return CMG_OK;
 }
 

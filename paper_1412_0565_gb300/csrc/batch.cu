@@ -123,7 +123,8 @@ struct BatchPiArgs {
     int *queue;           // work counter (zero at launch)
     const int *J;         // [G]   coarsest level per graph
     const int *agg;       // this level -> level + 1 (union ids)
-    const void *uc;       // T[n_{level+1}] normalised results of level + 1
+    const void *uc;       // normalised results of level + 1 (in that level's precision)
+    int uc_fp64;          // uc holds doubles (else floats)
     void *uo;             // T[n_level] normalised results (level > 0)
     double *uf;           // double[n_0] final vectors (level 0)
     void *vscr;           // T[2 n_level] iterates of graphs too large for shared memory
@@ -306,10 +307,12 @@ __global__ void __launch_bounds__(kBatchMaxThreads, 1) k_batch_pi(BatchPiArgs a)
         p0.B = ff_zero();
         p0.C = ff_zero();
         {
-            const T *ucT = reinterpret_cast<const T *>(a.uc);
             for (int i = gt; i < n; i += tg) {
                 const int old = a.perm[v0 + i];
-                const double xv = gauss ? gaussian_entry(a.seed, old - v0) : (double)ucT[a.agg[old]];
+                double xv;
+                if (gauss) xv = gaussian_entry(a.seed, old - v0);
+                else if (a.uc_fp64) xv = reinterpret_cast<const double *>(a.uc)[a.agg[old]];
+                else xv = (double)reinterpret_cast<const float *>(a.uc)[a.agg[old]];
                 const T xt = (T)xv;
                 X0[i] = xt;
                 if (fp64) {
@@ -816,11 +819,21 @@ static cmg_batch_shape_t default_shape(const BLevel &L) {
     return sh;
 }
 
+// Sweep precision of union level j.  In the FP32 form only level 0 sweeps in
+// FP32: it carries most of the bytes and the fewest sweeps.  The coarse
+// levels keep FP64 sweeps: each graph's coarse levels are small (its group
+// holds them in shared memory), and they run the longest sweep chains
+// (thousands of sweeps), along which FP32 rounding accumulates in slowly
+// converging components that the finer levels inherit.
+static int level_fp32(const cmg_batch_s *b, int j) {
+    return (b->opts.precision == CMG_PRECISION_FP32_SWEEP && j == 0) ? 1 : 0;
+}
+
 // Workspace of level j for its current shape: the fallback iterate buffers
 // are allocated only if some listed graph does not fit in shared memory.
 static cmg_status_t level_workspace(cmg_batch_s *b, int j, cudaStream_t s) {
     BLevel &L = b->lv[j];
-    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+    const int fp32 = level_fp32(b, j);
     const size_t esz = fp32 ? sizeof(float) : sizeof(double);
     DeviceInfo di;
     CMG_TRY(device_info(&di));
@@ -848,7 +861,7 @@ static cmg_status_t launch_part(cmg_batch_s *b, int j, int force_k, cudaStream_t
                                 int count, int *queue, const cmg_batch_shape_t &shape, int smem_group) {
     BLevel &L = b->lv[j];
     if (count <= 0) return CMG_OK;
-    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+    const int fp32 = level_fp32(b, j);
     const cmg_options_t &o = b->opts;
     BatchKernel kern = batch_kernel(fp32, L.lay.col16, shape.lanes_per_row);
     const int threads = threads_for_gpc(shape);
@@ -881,6 +894,7 @@ static cmg_status_t launch_part(cmg_batch_s *b, int j, int force_k, cudaStream_t
     a.J = b->dJ;
     a.agg = L.agg;
     a.uc = (j + 1 < (int)b->lv.size()) ? b->lv[j + 1].u : nullptr;
+    a.uc_fp64 = (j + 1 < (int)b->lv.size()) ? !level_fp32(b, j + 1) : 1;
     a.uo = L.u;
     a.uf = b->uf;
     a.vscr = L.vscr;
@@ -960,8 +974,8 @@ static cmg_status_t enqueue_solve(cmg_batch_s *b, int force_k, cudaStream_t s) {
 // Sweep layout of union level j (see SweepLayout).
 static cmg_status_t build_layout(cmg_batch_s *b, int j, cudaStream_t s, size_t *bytes) {
     BLevel &L = b->lv[j];
-    return build_sweep_layout(b->G, L.voff, L.hvoff, L.n, L.rp, L.col, L.w,
-                              b->opts.precision == CMG_PRECISION_FP32_SWEEP, &L.lay, bytes, s);
+    return build_sweep_layout(b->G, L.voff, L.hvoff, L.n, L.rp, L.col, L.w, level_fp32(b, j), &L.lay,
+                              bytes, s);
 }
 
 // Level lists: graphs with J >= j, ordered by decreasing n + nnz on level j.
@@ -971,7 +985,7 @@ static cmg_status_t build_lists(cmg_batch_s *b, cudaStream_t s) {
         BLevel &L = b->lv[j];
         std::vector<int> ids;
         L.max_vbytes = L.max_cbytes = 0;
-        const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+        const int fp32 = level_fp32(b, j);
         const long long esz = fp32 ? 4 : 8;
         for (int q = 0; q < G; q++) {
             if (b->J[q] < j) continue;
@@ -1151,11 +1165,10 @@ static cmg_status_t build_batch(cmg_batch_s *b, const int64_t *offs, const int64
         if (b->J[q] < 0) b->J[q] = (int)b->lv.size() - 1;
     // ---- solve workspace
     const int L = (int)b->lv.size();
-    const int fp32 = o.precision == CMG_PRECISION_FP32_SWEEP;
-    const size_t esz = fp32 ? sizeof(float) : sizeof(double);
     size_t bytes = 0;
     for (int j = 0; j < L; j++) {
         BLevel &V = b->lv[j];
+        const size_t esz = level_fp32(b, j) ? sizeof(float) : sizeof(double);
         bytes += sizeof(int) * ((size_t)V.n + 1) + (sizeof(int) + sizeof(double)) * (size_t)V.nnz;
         bytes += sizeof(int) * (G + 1) + sizeof(double) * G;
         if (V.agg) bytes += sizeof(int) * (size_t)V.n;
@@ -1440,7 +1453,7 @@ extern "C" cmg_status_t cmg_batch_config(cmg_batch_t b, int32_t level, int32_t s
     cmg_status_t st = level_workspace(b, level, b->stream);
     if (st == CMG_OK) {
         // the shape must be launchable
-        const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
+        const int fp32 = level_fp32(b, level);
         int per_sm = 0;
         const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
             &per_sm, (const void *)batch_kernel(fp32, b->lv[level].lay.col16, shape->lanes_per_row), threads_for_gpc(*shape),
@@ -1486,7 +1499,6 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
     CMG_CUDA(cudaEventCreate(&e0));
     CMG_CUDA(cudaEventCreate(&e1));
     cmg_status_t st = CMG_OK;
-    const int fp32 = b->opts.precision == CMG_PRECISION_FP32_SWEEP;
     // 2. per level, coarse to fine (a level's order uses the replayed counts
     // of the level below it), time the candidate shapes
     auto time_shape = [&](int j, const cmg_batch_shape_t &sh, float *ms) -> cmg_status_t {
@@ -1495,7 +1507,7 @@ extern "C" cmg_status_t cmg_batch_autotune(cmg_batch_t b, void *stream) {
         CMG_TRY(level_workspace(b, j, s));
         int per_sm = 0;
         CMG_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-            &per_sm, (const void *)batch_kernel(fp32, V.lay.col16, sh.lanes_per_row), threads_for_gpc(sh),
+            &per_sm, (const void *)batch_kernel(level_fp32(b, j), V.lay.col16, sh.lanes_per_row), threads_for_gpc(sh),
             (size_t)V.smem_group * sh.graphs_per_cta));
         if (per_sm < 1) {
             *ms = 1e30f;

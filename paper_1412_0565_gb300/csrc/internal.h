@@ -201,6 +201,7 @@ struct PiRun {
     double tol;
     uint64_t seed;
     const void *coarse_bufs[3];
+    int coarse_fp64;                 // the coarse level's iterates are doubles
     const PiResult *coarse_res;
     const int *coarse_agg;           // agg of this level onto the coarse level
     const int *coarse_inv;           // the coarse level's layout order (nullptr: natural)

@@ -91,6 +91,7 @@ struct PiArgs {
     uint64_t seed;
     int start;              // 0 Gaussian, 1 prolongation, 2 explicit
     const void *cbuf[3];    // coarse ring (start = 1)
+    int cfp64;              // the coarse ring holds doubles (else floats)
     const PiResult *cres;
     const int *agg;
     const double *x_init;   // start = 2
@@ -119,13 +120,17 @@ struct PiArgs {
 
 // Start value of row i: Gaussian (Alg. 1 Step 2), prolongation (I^T y of
 // Alg. 1 Step 3) of the coarse result, or an explicit vector.
-template <typename T>
-__device__ __forceinline__ double start_value(const PiArgs &a, int i, const T *cb, double cmu,
+// The coarse ring has the coarse level's own sweep precision (a level held in
+// one CTA keeps FP64 sweeps in the FP32 form).
+__device__ __forceinline__ double start_value(const PiArgs &a, int i, const void *cb, double cmu,
                                               double cinv) {
     if (a.start == 0) return gaussian_entry(a.seed, i);
     if (a.start == 1) {
         const int c = a.agg[i];
-        return ((double)cb[a.cinvp ? a.cinvp[c] : c] - cmu) * cinv;
+        const int k = a.cinvp ? a.cinvp[c] : c;
+        const double v = a.cfp64 ? reinterpret_cast<const double *>(cb)[k]
+                                 : (double)reinterpret_cast<const float *>(cb)[k];
+        return (v - cmu) * cinv;
     }
     return a.x_init[i];
 }
@@ -317,17 +322,17 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
     // ---------------------------------------------------------- start phase
     // y_0 (and g - d_i for the FP64 form); then one blocking reduction.
     {
-        const T *cb = nullptr;
+        const void *cb = nullptr;
         double cmu = 0.0, cinv = 0.0;
         if (a.start == 1) {
-            cb = (const T *)a.cbuf[a.cres->buf];
+            cb = a.cbuf[a.cres->buf];
             cmu = a.cres->mu;
             cinv = a.cres->inv_s;
         }
         // start sums: A = sum y_0 (not small after a prolongation), B = sum y_0^2
         Part acc = part_zero();
         for (int i = r0 + tid; i < r1; i += blockDim.x) {
-            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
+            const T xt = (T)start_value(a, i, cb, cmu, cinv);
             ring0[i] = xt;
             if (fp64) {
                 double d = 0.0;
@@ -601,17 +606,17 @@ __global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 
 
     // ---------------------------------------------------------- start phase
     {
-        const T *cb = nullptr;
+        const void *cb = nullptr;
         double cmu = 0.0, cinv = 0.0;
         if (a.start == 1) {
-            cb = (const T *)a.cbuf[a.cres->buf];
+            cb = a.cbuf[a.cres->buf];
             cmu = a.cres->mu;
             cinv = a.cres->inv_s;
         }
         Part acc = part_zero();
         for (int p = r0 + tid; p < r1; p += blockDim.x) {
             const int old = a.perm[p];
-            const T xt = (T)start_value<T>(a, old, cb, cmu, cinv);
+            const T xt = (T)start_value(a, old, cb, cmu, cinv);
             ring0[p] = xt;
             if (fp64) {
                 double d = 0.0;
@@ -896,16 +901,16 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
         }
     }
     {
-        const T *cb = nullptr;
+        const void *cb = nullptr;
         double cmu = 0.0, cinv = 0.0;
         if (a.start == 1) {
-            cb = (const T *)a.cbuf[a.cres->buf];
+            cb = a.cbuf[a.cres->buf];
             cmu = a.cres->mu;
             cinv = a.cres->inv_s;
         }
         Part acc = part_zero();
         for (int i = tid; i < n; i += blockDim.x) {
-            const T xt = (T)start_value<T>(a, i, cb, cmu, cinv);
+            const T xt = (T)start_value(a, i, cb, cmu, cinv);
             ring0[i] = xt;
             if (fp64) {
                 double d = 0.0;
@@ -1248,6 +1253,7 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.start = run.x_init ? 2 : (run.coarse_res ? 1 : 0);
     for (int k = 0; k < 3; k++) {
         a.cbuf[k] = run.coarse_bufs[k];
+        a.cfp64 = run.coarse_fp64;
         a.buf[k] = run.bufs[k];
     }
     a.cres = run.coarse_res;

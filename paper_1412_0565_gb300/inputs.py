@@ -19,7 +19,7 @@ import numpy as np
 __all__ = [
     "csr_from_edges", "grid2d", "grid3d", "path", "cycle", "complete", "star",
     "random_connected", "chung_lu", "rgg", "barabasi_albert", "largest_component",
-    "batch_graphs", "concat_csr", "serving_sizes", "serving_graphs", "hub_grid",
+    "batch_graphs", "batch_graph", "concat_csr", "serving_sizes", "serving_graphs", "hub_grid",
 ]
 
 
@@ -335,6 +335,11 @@ def batch_sizes(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1
     """Vertex counts of a mixed batch: log-uniform in [lo, hi]."""
     rng = np.random.default_rng(seed)
     return np.exp(rng.uniform(np.log(lo), np.log(hi), size=count)).astype(np.int64)
+
+
+def batch_graph(i: int, count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412):
+    """Graph i of batch_graphs(count, lo, hi, seed), built alone."""
+    return _family_graph(i, int(batch_sizes(count, lo, hi, seed)[i]), seed)
 
 
 def batch_graphs(count: int = 4096, lo: int = 500, hi: int = 20000, seed: int = 1412,

@@ -259,3 +259,20 @@ def test_batch_split_levels_match_oracle():
             uq = u[offs[q]:offs[q + 1]]
             assert abs(lam[q] - ref[1]) <= 1e-6 * abs(ref[1]), q
             assert angle(uq, ref[0]) <= 1e-4, q
+
+
+def test_batch_fp32_on_graphs_with_long_coarse_sweep_chains():
+    """Graphs of the 4,096-graph mixed batch whose coarse levels run about
+    12,000 sweeps: with FP32 sweeps on every union level their lambda2 missed
+    1e-6 of the oracle (rounding accumulated along those chains).  Only union
+    level 0 sweeps in FP32; the replayed result meets the stated accuracy."""
+    graphs = [inputs.batch_graph(i) for i in (671, 1814, 2267, 2933, 2889, 0, 1, 2)]
+    rp, col, w, offs = inputs.concat_csr(graphs)
+    refs = [oracle.Hierarchy(*g, seed=SEED).solve() for g in graphs]
+    with cmg.Batch(offs, rp, col, w, seed=SEED, precision="fp32", schedule="replay") as b:
+        b.set_replay([r["sweeps"].tolist() for r in refs])
+        u, lam, res, _ = b.fiedler()
+        for q, ref in enumerate(refs):
+            assert b.stats(q)["sweeps"] == ref["sweeps"].tolist()
+            assert abs(lam[q] - ref["lam"]) <= 1e-6 * abs(ref["lam"]), q
+            assert angle(u[offs[q]:offs[q + 1]], ref["u"]) <= 1e-4, q

@@ -129,15 +129,31 @@ def test_schedules_match_oracle(schedule):
     assert lam == pytest.approx(ref["lam"], rel=LAM_TOL)
 
 
-@pytest.mark.parametrize("name", ["grid64_unit", "grid3d_small", "random", "rgg", "ba", "chung_lu"])
+# Graphs of the 4,096-graph mixed batch (preferential-attachment graphs with
+# about 12,000 sweeps on some coarse level, and a random geometric graph) on
+# which FP32 sweeps on every level missed lambda2 within 1e-6 of the oracle:
+# the rounding accumulated along the coarse levels' long sweep chains.
+FP32_HARD = {f"batch4096_{i}": (lambda i=i: inputs.batch_graph(i)) for i in (671, 1814, 2267, 2933, 2889)}
+
+
+@pytest.mark.parametrize("name", ["grid64_unit", "grid3d_small", "random", "rgg", "ba", "chung_lu"]
+                         + sorted(FP32_HARD))
 def test_fp32_sweep_form_accuracy(name):
-    """FP32 sweeps with FP64 reductions and a final FP64 recompute, against the
-    FP64 oracle run with the same per-level sweep counts."""
-    rp, col, w = CASES[name]()
-    h = cmg.Hierarchy(rp, col, w, seed=1412, precision="fp32")
-    u32, lam32, st32 = h.fiedler()
+    """FP32 sweeps (on the levels that carry the bytes) with float-float
+    reductions and a final FP64 recompute, against the FP64 oracle run with
+    the same per-level sweep counts (the oracle's own tolerance-mode counts,
+    replayed), so the comparison measures precision alone: lambda2 within
+    1e-6 relative, vector within 1e-4 rad."""
+    rp, col, w = (CASES.get(name) or FP32_HARD[name])()
     oh = oracle.Hierarchy(rp, col, w, seed=1412)
-    ref = oh.solve(schedule="replay", replay=st32["sweeps"])
+    ref = oh.solve()
+    h = cmg.Hierarchy(rp, col, w, seed=1412, precision="fp32", schedule="replay",
+                      replay_sweeps=ref["sweeps"].tolist())
+    u32, lam32, st32 = h.fiedler()
+    prec = h.level_precision()
+    h.close()
+    assert st32["sweeps"] == ref["sweeps"].tolist()
+    assert all((p == "fp32") == (n > 65536) for p, n in zip(prec, st32["n"]))
     assert abs(lam32 - ref["lam"]) <= 1e-6 * abs(ref["lam"])
     assert angle(u32, ref["u"]) <= 1e-4
 
