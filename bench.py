@@ -4,7 +4,11 @@ A step is one pass of the whole method (Alg. 1): cmg_setup (heavy edge
 coarsening + Galerkin products on every level) and cmg_fiedler (coarsest
 solve, prolongation and power iteration on every level, final vector,
 Rayleigh quotient and residual) on the synthetic 100x100x100 grid with
-U[0.5, 1.5] edge weights (seed 1412), inputs resident in device memory.
+U[0.5, 1.5] edge weights (seed 1412), inputs resident in device memory.  The
+headline is the FP64 form, the paper's arithmetic; the FP32-sweep form, the
+64x64 grid, the 4,096-graph batch, the request loop and the Chung-Lu graph
+are reported under their own keys, each result's accuracy against the CPU
+oracle.
 
 Prints ONE JSON line (rank 0).  `--impl reference` times the CPU oracle (the
 plain sequential FP64 restatement of the method) on the same workload.
@@ -33,8 +37,15 @@ WORKLOAD = {"workload": "grid3d_100x100x100_uniform[0.5,1.5]_seed1412", "n": 1_0
             "coarse_size": 25}
 # The timed step is one whole CMG solve; inputs (71 MB of CSR) are smaller than
 # L2 (129 MB), so L2 is flushed between timed steps.
+L2_NOTE = "inputs 71 MB < L2: a 256 MB buffer is written between timed steps (flush)"
 METRIC = "Fiedler solves/s (CMG setup + solve, 3D grid 1M vertices)"
 UNIT = "solves/s"
+
+
+def config(world: int) -> dict:
+    """The workload of both arms (identical dicts: the reference arm times the
+    oracle on exactly this configuration)."""
+    return dict(WORKLOAD, l2=L2_NOTE, parallelism=f"replicas{world}")
 
 
 def make_graph():
@@ -48,6 +59,13 @@ def sweep_bytes(n, nnz, fp32=False):
     if fp32:
         return 8 * nnz + 12 * n
     return 12 * nnz + 20 * n
+
+
+def sweep_flops_fp64(n, nnz):
+    """Algorithmic FP64 flops of one FP64 sweep: an FMA per stored entry, and
+    per row the diagonal FMA (g - d_i) x_i, the shift and scale (2), and the
+    sums y, y^2, y x_prev of the stop test (5)."""
+    return 2 * nnz + 9 * n
 
 
 def level_launch_bytes(n, nnz, sweeps, n_coarse, fp32=False):
@@ -116,8 +134,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-PROFILE = os.path.join(ROOT, "profiles", "k_power_sell_f32_grid3d_100_level0.md")
+PROFILES = {"fp64": os.path.join(ROOT, "profiles", "k_power_sell_f64_grid3d_100_level0.md"),
+            "fp32": os.path.join(ROOT, "profiles", "k_power_sell_f32_grid3d_100_level0.md")}
 NOMINAL_HBM_GBS = 7900.0   # GB300 HBM3e nominal bandwidth (context beside the measured copy peak)
+# FP64 pipe: 2 FMA per SM per clock (the nominal 1.25 TFLOP/s of a 152-SM GB300 at 2.07 GHz)
+FP64_FMA_PER_SM_CLK = 2
+SMS = 152
 PROFILED_SOURCES = [os.path.join(ROOT, "paper_1412_0565_gb300", "csrc", f)
                     for f in ("refine.cu", "pi_common.cuh", "ffloat.cuh")]
 
@@ -137,11 +159,11 @@ def kernel_fingerprint():
     return hashlib.sha256("\n".join(parts).encode()).hexdigest()[:16]
 
 
-def profiled_traffic():
+def profiled_traffic(prec):
     """DRAM bytes per level-0 launch from the committed ncu summary, or None
     when the kernel code changed since that capture."""
     try:
-        text = open(PROFILE).read()
+        text = open(PROFILES[prec]).read()
         h = kernel_fingerprint()
         fields = dict(line.strip("- ").split(": ", 1) for line in text.splitlines()
                       if line.startswith("- ") and ": " in line)
@@ -153,16 +175,27 @@ def profiled_traffic():
 
 
 def cpu_info():
+    """CPU model and core count of this host (lscpu, then /proc/cpuinfo)."""
     model = ""
     try:
-        with open("/proc/cpuinfo") as f:
-            for l in f:
-                if l.lower().startswith(("model name", "cpu model")):
-                    model = l.split(":", 1)[1].strip()
-                    break
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        f = dict(l.split(":", 1) for l in out.splitlines() if ":" in l)
+        f = {k.strip(): v.strip() for k, v in f.items()}
+        model = f.get("Model name", "")
+        if f.get("Vendor ID"):
+            model = f"{f['Vendor ID']} {model}".strip()
     except Exception:
         pass
-    return model or os.uname().machine
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for l in fh:
+                    if l.lower().startswith(("model name", "cpu model", "cpu part")):
+                        model = l.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"model": model or os.uname().machine, "nproc": os.cpu_count(), "arch": os.uname().machine}
 
 
 def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
@@ -207,17 +240,62 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     total = sum(times)
     value = args.steps / total
+    ci = cpu_info()
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": dict(WORKLOAD, l2="input 71 MB < L2; CPU run"),
+        "data": "synthetic", "config": config(args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} full CMG solves (setup+solve) of the 1M-vertex "
-                                   f"grid, single-threaded C oracle, {cpu_info()}"},
+                         "cpu_model": ci["model"], "nproc": ci["nproc"],
+                         "sample": f"{args.steps} full CMG solves (setup+solve, FP64) of the 1M-vertex "
+                                   f"grid, single-threaded C oracle on one of {ci['nproc']} cores "
+                                   f"({ci['model']})"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def _angle(a, b):
+    c = abs(float(np.dot(a, b))) / (np.linalg.norm(a) * np.linalg.norm(b))
+    return float(np.arccos(min(1.0, c)))
+
+
+def _vec_err(u, ref):
+    if np.dot(u, ref) < 0:
+        u = -u
+    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+
+# ---------------------------------------------------------------- oracle jobs (spawned pool)
+def _oracle_job(job):
+    """One oracle solve in a worker process: ("batch", i) graph i of the
+    4,096-graph batch; ("graph", name, rp, col, w) an explicit graph.
+    Returns (key, sweeps, u, lambda, residual, seconds)."""
+    import oracle
+    from paper_1412_0565_gb300 import inputs
+    t0 = time.perf_counter()
+    if job[0] == "batch":
+        g = inputs.batch_graph(job[1])
+        key = job[1]
+    elif job[0] == "chung_lu":
+        g = inputs.chung_lu(job[1], seed=1412)
+        key = "chung_lu"
+    else:
+        g = job[2:]
+        key = job[1]
+    r = oracle.Hierarchy(*g, seed=1412).solve()
+    return key, r["sweeps"], r["u"], r["lam"], r["res"], time.perf_counter() - t0
+
+
+def run_oracle_jobs(jobs, workers):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    out = {}
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        for key, sw, u, lam, res, dt in ex.map(_oracle_job, jobs, chunksize=4):
+            out[key] = {"sweeps": sw, "u": u, "lam": lam, "res": res, "s": dt}
+    return out
 
 
 def run_gpu(args):
@@ -251,15 +329,16 @@ def run_gpu(args):
         """Timed steps of setup + solve with device-resident inputs."""
         opts = cmg.options(seed=1412, timing=1, precision=precision)
         u = torch.empty(n, dtype=torch.float64, device="cuda")
-        kinds = {}
+        info = {}
 
         def step(mid=None):
             h = cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid)
             if mid is not None:
                 mid.record(stream)
             _, lam, st = h.fiedler(u_out=u, stream=sid)
-            if not kinds:
-                kinds["k"] = h.level_kernels()
+            if not info:
+                info["kinds"] = h.level_kernels()
+                info["prec"] = h.level_precision()
             h.close()
             return lam, st
 
@@ -289,24 +368,13 @@ def run_gpu(args):
                 "setup_ms": statistics.median(setup_ms),
                 "solve_ms": statistics.median(a - b for a, b in zip(step_ms, setup_ms)),
                 "stats": stats, "launches": launches, "u": u.cpu().numpy(), "lam": lam,
-                "kinds": kinds["k"]}
+                "kinds": info["kinds"], "prec": info["prec"]}
 
     with ClockSampler(local) as clk:
-        r32 = measure("fp32", args.steps, args.warmup)
         r64 = measure("fp64", args.steps, args.warmup)
+        r32 = measure("fp32", args.steps, args.warmup) if not args.no_fp32 else None
     clocks = clk.summary()
-
-    # ---- roofline of the dominant kernel: the level-0 power-iteration launch
-    def roofline(r, fp32):
-        st0 = r["stats"][-1]
-        ns, nnzs, sweeps = st0["n"], st0["nnz"], st0["sweeps"]
-        L = len(ns)
-        ms0 = statistics.median(s["level_ms"][0] for s in r["stats"])
-        by0 = level_launch_bytes(ns[0], nnzs[0], sweeps[0], ns[1] if L > 1 else 0, fp32)
-        tot_b = sum(level_launch_bytes(ns[j], nnzs[j], sweeps[j], ns[j + 1] if j + 1 < L else 0, fp32)
-                    for j in range(L))
-        tot_ms = statistics.median(sum(s["level_ms"]) for s in r["stats"])
-        return ms0, by0, tot_b, tot_ms, st0
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
 
     peaks = {}
     try:
@@ -318,62 +386,103 @@ def run_gpu(args):
     peak_src = "measured" if hbm_peak else "fallback"
     if not hbm_peak:
         hbm_peak = 6800.0
-    ms0, by0, tot_b, tot_ms, st32 = roofline(r32, True)
-    achieved0 = by0 / (ms0 * 1e-3) / 1e9
-    traffic, traffic_note = profiled_traffic()
-    roof = {"bound": "hbm", "kernel": "k_power_sell<float, int>, level-0 launch",
-            "achieved": achieved0, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-            "frac": achieved0 / hbm_peak, "traffic": traffic, "traffic_note": traffic_note,
-            "nominal_peak": NOMINAL_HBM_GBS, "frac_of_nominal": achieved0 / NOMINAL_HBM_GBS,
-            "bytes_per_launch": by0,
-            "launch_ms": ms0, "sweeps_per_launch": st32["sweeps"][0],
-            "all_levels": {"bytes": tot_b, "ms": tot_ms, "achieved": tot_b / (tot_ms * 1e-3) / 1e9}}
-    ms0_64, by0_64, tot_b64, tot_ms64, st64 = roofline(r64, False)
 
-    # accuracy of the FP32-sweep form against the plain FP64 form
-    u32, u64 = r32["u"], r64["u"]
-    cosang = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
-    acc = {"lambda2_rel_diff": abs(r32["lam"] - r64["lam"]) / abs(r64["lam"]),
-           "angle_rad": float(np.arccos(min(1.0, cosang))),
-           "note": "FP32-sweep result vs plain FP64 GPU result, tolerance-mode sweep counts differ"}
+    def level0(r, fp32):
+        st0 = r["stats"][-1]
+        ns, nnzs, sweeps = st0["n"], st0["nnz"], st0["sweeps"]
+        L = len(ns)
+        ms0 = statistics.median(s["level_ms"][0] for s in r["stats"])
+        by0 = level_launch_bytes(ns[0], nnzs[0], sweeps[0], ns[1] if L > 1 else 0, fp32)
+        tot_b = sum(level_launch_bytes(ns[j], nnzs[j], sweeps[j], ns[j + 1] if j + 1 < L else 0,
+                                       r["prec"][j] == "fp32") for j in range(L))
+        tot_ms = statistics.median(sum(s["level_ms"]) for s in r["stats"])
+        return ms0, by0, tot_b, tot_ms, st0
 
-    # ---- end to end through the public API with host buffers (FP32 form)
-    e2e_ms = []
-    # inputs and the result buffer in pinned host memory (filled once, outside
-    # the timed region), so the copies inside it are plain DMA transfers
-    try:
-        rp_h, col_h, w_h, hu = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-                                for a in (rp, col, w, np.empty(n, dtype=np.float64)))
-        pinned = True
-    except Exception:
-        rp_h, col_h, w_h, hu = (np.ascontiguousarray(a) for a in (rp, col, w, np.empty(n, dtype=np.float64)))
-        pinned = False
-    for _ in range(max(2, min(args.steps, 5))):
-        flush.zero_()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        h = cmg.Hierarchy(rp_h, col_h, w_h, seed=1412, precision="fp32", stream=sid)
-        h.fiedler(u_out=hu, stream=sid)
-        h.close()
-        e1.record(stream)
-        e1.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    e2e_val = whole_job_rate(len(e2e_ms), sum(e2e_ms), world)
+    def roofline(r, fp32):
+        """The dominant kernel: the level-0 power-iteration launch.  FP64
+        sweeps are bound by the FP64 pipe on this GPU (at its peak a sweep's
+        FP64 work takes longer than its bytes at the HBM copy peak); FP32
+        sweeps by memory."""
+        ms0, by0, tot_b, tot_ms, st0 = level0(r, fp32)
+        n0, nnz0, k0 = st0["n"][0], st0["nnz"][0], st0["sweeps"][0]
+        gbs = by0 / (ms0 * 1e-3) / 1e9
+        traffic, tnote = profiled_traffic("fp32" if fp32 else "fp64")
+        hbm = {"achieved": gbs, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+               "frac": gbs / hbm_peak, "frac_of_nominal": gbs / NOMINAL_HBM_GBS}
+        common = {"bytes_per_launch": by0, "launch_ms": ms0, "sweeps_per_launch": k0,
+                  "traffic": traffic, "traffic_note": tnote,
+                  "l2_resident": by0 / max(k0, 1) < 126e6,
+                  "note": ("the level's sweep stream fits in L2 (129 MB): after the first sweep it "
+                           "is served from L2, so the GB/s is an effective streaming rate, not DRAM "
+                           "traffic (traffic = ncu DRAM bytes)"),
+                  "all_levels": {"bytes": tot_b, "ms": tot_ms,
+                                 "achieved_gbs": tot_b / (tot_ms * 1e-3) / 1e9}}
+        if fp32:
+            return dict({"bound": "hbm", "kernel": "k_power_sell<float, int>, level-0 launch"}, **hbm,
+                        **common)
+        flops = k0 * sweep_flops_fp64(n0, nnz0)
+        peak_tf = FP64_FMA_PER_SM_CLK * 2 * SMS * sm_mhz * 1e6 / 1e12
+        tf = flops / (ms0 * 1e-3) / 1e12
+        return dict({"bound": "alu", "kernel": "k_power_sell<double, int>, level-0 launch",
+                     "achieved": tf, "peak": peak_tf, "unit": "TFLOP/s", "frac": tf / peak_tf,
+                     "peak_source": "derived: 2 FP64 FMA per SM per clock x 152 SMs x the median SM "
+                                    "clock of the run (nominal 1.25 TFLOP/s)",
+                     "flops_per_launch": flops,
+                     "hbm": hbm}, **common)
 
-    batch = None
-    if not args.no_batch and world == 1:
-        batch = run_batch(args, stream, flush)
-    serving = None
-    if not args.no_serving and world == 1:
-        serving = run_serving(args)
-    chung_lu = None
-    if not args.no_chung_lu and world == 1:
-        chung_lu = run_chung_lu(args, stream, flush)
+    def e2e(precision):
+        """The public API with host buffers: host->device copy of the CSR and
+        device->host copy of the vector inside the timed region."""
+        ms = []
+        try:
+            rp_h, col_h, w_h, hu = (torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+                                    for a in (rp, col, w, np.empty(n, dtype=np.float64)))
+            pinned = True
+        except Exception:
+            rp_h, col_h, w_h, hu = (np.ascontiguousarray(a) for a in (rp, col, w, np.empty(n, dtype=np.float64)))
+            pinned = False
+        for _ in range(max(3, min(args.steps, 8))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h = cmg.Hierarchy(rp_h, col_h, w_h, seed=1412, precision=precision, stream=sid)
+            h.fiedler(u_out=hu, stream=sid)
+            h.close()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return {"value": whole_job_rate(len(ms), sum(ms), world), "unit": UNIT,
+                "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n,
+                "host_memory": "pinned" if pinned else "pageable", "steps": len(ms)}
+
+    roof64 = roofline(r64, False)
+    e2e64 = e2e("fp64") if not args.no_e2e else None
+    fp32 = None
+    if r32 is not None:
+        ms0, by0, tot_b, tot_ms, st32 = level0(r32, True)
+        fp32 = {"value": r32["value"], "unit": UNIT, "ms_per_step": r32["ms_per_step"],
+                "dtype": "f32 sweeps on levels of at least 2^20 stored entries, f64 sweeps below; "
+                         "float-float stop/mean/norm sums; f64 last level-0 sweep and Rayleigh quotient",
+                "latency_ms": {"p50": r32["p50_ms"], "p99": r32["p99_ms"]},
+                "split_ms": {"setup": r32["setup_ms"], "solve": r32["solve_ms"]},
+                "levels": {"sweeps": st32["sweeps"], "precision": r32["prec"],
+                           "kernel": [KERNEL_KIND[k] for k in r32["kinds"][0]],
+                           "level_ms": [round(x, 4) for x in st32["level_ms"]]},
+                "lambda2": st32["lambda2"], "residual": st32["residual"],
+                "roofline": roofline(r32, True),
+                "e2e": e2e("fp32") if not args.no_e2e else None,
+                "gpu_launches": r32["launches"]}
+
+    c1 = run_c1(args, stream, flush) if (not args.no_c1 and world == 1) else None
+    batch = run_batch(args, stream, flush) if (not args.no_batch and world == 1) else None
+    serving = run_serving(args) if (not args.no_serving and world == 1) else None
+    chung_lu = run_chung_lu(args, stream, flush) if (not args.no_chung_lu and world == 1) else None
 
     if rank == 0:
         cpu = None
+        ci = cpu_info()
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
@@ -383,38 +492,42 @@ def run_gpu(args):
                 reps += 1
             dt = time.perf_counter() - t0
             cpu = {"value": reps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "cpu_model": ci["model"], "nproc": ci["nproc"],
                    "sample": f"{reps} full CMG solves (setup+solve, FP64) of the same 1M-vertex grid, "
-                             f"single-threaded C oracle on {cpu_info()}"}
+                             f"single-threaded C oracle on one of {ci['nproc']} cores ({ci['model']})"}
+        # ---- accuracy against the CPU oracle (spawned worker processes, after
+        # every timed region)
+        accuracy = None
+        if world == 1 and not args.no_oracle_checks:
+            accuracy = oracle_checks(args, (rp, col, w), r64, r32, batch, chung_lu, stream)
+        st64 = r64["stats"][-1]
+        if batch:
+            for k in [k for k in batch if k.startswith("_")]:
+                batch.pop(k)
         line = {
-            "metric": METRIC, "value": r32["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": max(3, args.warmup), "ms_per_step": r32["ms_per_step"],
+            "metric": METRIC, "value": r64["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": r64["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32 sweeps, f64 final sweep / Rayleigh quotient, float-float reductions",
+            "dtype": "f64",
+            "dtype_note": "f64 sweeps, f64 Rayleigh quotient and residual; the stop cosine, mean and norm "
+                          "sums in float-float (about 48 bits: the 1 - 1e-8 cosine test is resolved to "
+                          "about 1e-14)",
             "data": "synthetic",
-            "config": dict(WORKLOAD, precision="fp32-sweep",
-                           l2="256 MB buffer written between timed steps (flush)",
-                           parallelism=f"replicas{world}"),
-            "latency_ms": {"p50": r32["p50_ms"], "p99": r32["p99_ms"]},
-            "split_ms": {"setup": r32["setup_ms"], "solve": r32["solve_ms"]},
-            "levels": {"n": st32["n"], "nnz": st32["nnz"], "sweeps": st32["sweeps"],
-                       "kernel": [KERNEL_KIND[k] for k in r32["kinds"][0]],
-                       "level_ms": [round(x, 4) for x in st32["level_ms"]]},
-            "lambda2": st32["lambda2"], "residual": st32["residual"],
-            "fp64": {"value": r64["value"], "ms_per_step": r64["ms_per_step"],
-                     "latency_ms": {"p50": r64["p50_ms"], "p99": r64["p99_ms"]},
-                     "split_ms": {"setup": r64["setup_ms"], "solve": r64["solve_ms"]},
-                     "sweeps": st64["sweeps"], "level_ms": [round(x, 4) for x in st64["level_ms"]],
-                     "lambda2": st64["lambda2"], "residual": st64["residual"],
-                     "level0_launch": {"ms": ms0_64, "bytes": by0_64,
-                                       "achieved_gbs": by0_64 / (ms0_64 * 1e-3) / 1e9},
-                     "gpu_launches": r64["launches"]},
-            "fp32_vs_fp64": acc,
-            "roofline": roof, "cpu_baseline": cpu,
-            "e2e": {"value": e2e_val, "unit": UNIT,
-                    "h2d_bytes_per_step": 8 * (n + 1) + 12 * nnz, "d2h_bytes_per_step": 8 * n,
-                    "host_memory": "pinned" if pinned else "pageable"},
-            "gpu_launches": r32["launches"],
+            "config": config(world),
+            "latency_ms": {"p50": r64["p50_ms"], "p99": r64["p99_ms"]},
+            "split_ms": {"setup": r64["setup_ms"], "solve": r64["solve_ms"]},
+            "levels": {"n": st64["n"], "nnz": st64["nnz"], "sweeps": st64["sweeps"],
+                       "kernel": [KERNEL_KIND[k] for k in r64["kinds"][0]],
+                       "level_ms": [round(x, 4) for x in st64["level_ms"]]},
+            "lambda2": st64["lambda2"], "residual": st64["residual"],
+            "roofline": roof64, "cpu_baseline": cpu,
+            "e2e": e2e64,
+            "gpu_launches": r64["launches"],
             "clocks": clocks,
+            "host": ci,
+            "fp32": fp32,
+            "accuracy_vs_oracle": accuracy,
+            "c1": c1,
             "batch": batch,
             "serving": serving,
             "chung_lu": chung_lu,
@@ -423,6 +536,188 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def oracle_checks(args, c2_graph, r64, r32, batch, chung_lu, stream):
+    """Every accuracy statement of the line, against the FP64 CPU oracle run
+    in spawned processes: the C2 vectors, all (or a seeded sample of) the
+    4,096 batch graphs, and a Chung-Lu graph of the same recipe small enough
+    for the oracle.  FP32 results are compared in replay mode (the oracle's
+    own per-level sweep counts replayed on the GPU: precision alone); FP64
+    results in tolerance mode (same counts expected)."""
+    import torch
+    from paper_1412_0565_gb300 import cmg, inputs
+    t0 = time.perf_counter()
+    G = args.batch_graphs if batch is not None else 0
+    if G and args.batch_oracle_sample and args.batch_oracle_sample < G:
+        idx = sorted(np.random.default_rng(1412).choice(G, args.batch_oracle_sample, replace=False).tolist())
+    else:
+        idx = list(range(G))
+    jobs = [("graph", "c2", *c2_graph)]
+    if args.cl_oracle_n:
+        jobs.append(("chung_lu", args.cl_oracle_n))
+    jobs += [("batch", i) for i in idx]
+    res = run_oracle_jobs(jobs, workers=max(1, min(16, (os.cpu_count() or 2) - 1)))
+    out = {"oracle_s": round(time.perf_counter() - t0, 1)}
+    # ---- C2: FP64 form in tolerance mode; FP32 form with the oracle's counts
+    o = res["c2"]
+    out["c2_fp64"] = {"vec_rel_err": _vec_err(r64["u"], o["u"]),
+                      "lambda2_rel_err": abs(r64["lam"] - o["lam"]) / abs(o["lam"]),
+                      "same_sweeps": r64["stats"][-1]["sweeps"] == o["sweeps"].tolist(),
+                      "gate": "vector <= 1e-10, lambda2 <= 1e-12"}
+    if r32 is not None:
+        rp, col, w = c2_graph
+        u32, lam32, _ = cmg.fiedler(rp, col, w, seed=1412, precision="fp32", schedule="replay",
+                                    replay_sweeps=o["sweeps"].tolist())
+        out["c2_fp32_replay"] = {"lambda2_rel_err": abs(lam32 - o["lam"]) / abs(o["lam"]),
+                                 "angle_rad": _angle(u32, o["u"]), "gate": "lambda2 <= 1e-6, angle <= 1e-4"}
+    # ---- batch: every sampled graph, FP64 batch (tolerance) and FP32 batch (replay)
+    if idx:
+        graphs = batch["_graphs"]
+        rp, col, w, offs = batch["_union"]
+        drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
+        sid = stream.cuda_stream
+        u64, lam64 = batch["_u64"], batch["_lam64"]
+        sw64 = batch["_sweeps64"]
+        # FP32 batch with the oracle's counts (graphs outside the sample keep
+        # the GPU FP64 counts; only the sample is compared)
+        reps = [list(s) for s in sw64]
+        for i in idx:
+            reps[i] = res[i]["sweeps"].tolist()
+        u_t = torch.empty(len(rp) - 1, dtype=torch.float64, device="cuda")
+        with cmg.Batch(offs, drp, dcol, dw, seed=1412, precision="fp32", schedule="replay", stream=sid) as b:
+            b.set_replay(reps)
+            _, lam32, _, _ = b.fiedler(u_out=u_t, stream=sid)
+        u32 = u_t.cpu().numpy()
+        with cmg.Batch(offs, drp, dcol, dw, seed=1412, precision="fp64", schedule="replay", stream=sid) as b:
+            b.set_replay(reps)
+            _, lam64r, _, _ = b.fiedler(u_out=u_t, stream=sid)
+        u64r = u_t.cpu().numpy()
+        rel64, vec64, rel32, ang32, same = [], [], [], [], 0
+        rel64r, vec64r, apart = [], [], []
+        for i in idx:
+            ref = res[i]
+            a, b_ = offs[i], offs[i + 1]
+            rel64r.append(abs(lam64r[i] - ref["lam"]) / abs(ref["lam"]))
+            vec64r.append(_vec_err(u64r[a:b_], ref["u"]))
+            if list(sw64[i]) != ref["sweeps"].tolist():
+                apart.append({"graph": int(i), "gpu_sweeps": list(sw64[i]), "oracle_sweeps": ref["sweeps"].tolist()})
+            rel64.append(abs(lam64[i] - ref["lam"]) / abs(ref["lam"]))
+            vec64.append(_vec_err(u64[a:b_], ref["u"]))
+            same += int(list(sw64[i]) == ref["sweeps"].tolist())
+            rel32.append(abs(lam32[i] - ref["lam"]) / abs(ref["lam"]))
+            ang32.append(_angle(u32[a:b_], ref["u"]))
+        rel32, ang32 = np.array(rel32), np.array(ang32)
+        out["batch_graphs_compared"] = len(idx)
+        out["batch_sample"] = "all graphs" if len(idx) == G else f"seeded sample of {len(idx)} of {G}"
+        out["batch_fp64_tolerance"] = {"vec_rel_err_max": max(vec64), "lambda2_rel_err_max": max(rel64),
+                                       "same_sweeps": same, "gate": "vector <= 1e-10, lambda2 <= 1e-12",
+                                       "within_gate": int(sum((v <= 1e-10) and (r <= 1e-12)
+                                                              for v, r in zip(vec64, rel64))),
+                                       "sweeps_apart": apart[:8],
+                                       "note": "a graph whose stop cosine lies within rounding of 1 - tol "
+                                               "on some level can stop one sweep apart from the oracle "
+                                               "(float-float vs sequential FP64 sums); the replay "
+                                               "comparison below takes the oracle's counts"}
+        out["batch_fp64_replay"] = {"vec_rel_err_max": max(vec64r), "lambda2_rel_err_max": max(rel64r),
+                                    "gate": "vector <= 1e-10, lambda2 <= 1e-12",
+                                    "within_gate": int(sum((v <= 1e-10) and (r <= 1e-12)
+                                                           for v, r in zip(vec64r, rel64r)))}
+        out["batch_fp32_replay"] = {"lambda2_rel_err_max": float(rel32.max()),
+                                    "lambda2_rel_err_p99": float(np.percentile(rel32, 99)),
+                                    "angle_max": float(ang32.max()), "gate": "lambda2 <= 1e-6, angle <= 1e-4",
+                                    "within_gate": int(((rel32 <= 1e-6) & (ang32 <= 1e-4)).sum())}
+        tol32 = batch.get("_lam32_tol")
+        if tol32 is not None:
+            rt = np.array([abs(tol32[i] - res[i]["lam"]) / abs(res[i]["lam"]) for i in idx])
+            at = np.array([_angle(batch["_u32_tol"][offs[i]:offs[i + 1]], res[i]["u"]) for i in idx])
+            out["batch_fp32_tolerance_mode"] = {
+                "lambda2_rel_err_max": float(rt.max()), "angle_max": float(at.max()),
+                "within_1e-6_and_1e-4": int(((rt <= 1e-6) & (at <= 1e-4)).sum()),
+                "note": "each form stops on its own cosine test: a stop one sweep earlier or later "
+                        "moves the vector by up to arccos(1 - tol) = 1.4e-4 rad (the stop rule's "
+                        "resolution), not by FP32 rounding; the replay comparison above isolates "
+                        "precision"}
+    # ---- Chung-Lu of the same recipe, small enough for the oracle
+    if args.cl_oracle_n:
+        o = res["chung_lu"]
+        g = inputs.chung_lu(args.cl_oracle_n, seed=1412)
+        nn = len(g[0]) - 1
+        with cmg.Hierarchy(*g, seed=1412, precision="fp64") as h:
+            u64c, l64c, st64c = h.fiedler()
+        with cmg.Hierarchy(*g, seed=1412, precision="fp32", schedule="replay",
+                           replay_sweeps=o["sweeps"].tolist()) as h:
+            u32c, l32c, _ = h.fiedler()
+            prec = h.level_precision()
+        d = np.add.reduceat(g[2], g[0][:-1])
+        bound = nn / (nn - 1) * float(d.min())
+        from oracle import gershgorin
+        gg = gershgorin(*g)
+        out["chung_lu_small"] = {
+            "workload": cl_workload(args.cl_oracle_n), "n": nn, "nnz": int(g[0][-1]),
+            "fp64_vs_oracle": {"vec_rel_err": _vec_err(u64c, o["u"]),
+                               "lambda2_rel_err": abs(l64c - o["lam"]) / abs(o["lam"]),
+                               "same_sweeps": st64c["sweeps"] == o["sweeps"].tolist()},
+            "fp32_replay_vs_oracle": {"lambda2_rel_err": abs(l32c - o["lam"]) / abs(o["lam"]),
+                                      "angle_rad": _angle(u32c, o["u"]), "level_precision": prec},
+            "oracle_lambda": o["lam"], "oracle_residual": o["res"], "g": gg,
+            "lambda2_upper_bound": bound,
+            "per_sweep_change_bound": bound / gg,
+            "fp32_unit_roundoff": 2.0 ** -24,
+            "note": ("lambda2 <= n/(n-1) min_i d_i (Fiedler's bound) is far below the returned "
+                     "Rayleigh quotient: the cosine stop ends the power iteration as soon as a sweep "
+                     "turns the vector by less than arccos(1 - tol), i.e. once the Rayleigh quotient "
+                     "is below about g sqrt(2 tol); with g / lambda2 of order 1e5 and more, the "
+                     "oracle and both GPU forms stop there alike (the method's behaviour, not a "
+                     "precision effect); per sweep the Fiedler component changes by at most "
+                     "lambda2 / g relative, a few FP32 ulps")}
+    return out
+
+
+KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled"}
+
+
+def run_c1(args, stream, flush):
+    """Config 1: the 64 x 64 unit grid (FP64): solves/s, latency, and the
+    result against the closed form (lambda2 = 2 - 2 cos(pi/64), double) and
+    the oracle."""
+    import torch
+    import oracle
+    from paper_1412_0565_gb300 import cmg, inputs
+    rp, col, w = inputs.grid2d(64, 64, "unit")
+    n = len(rp) - 1
+    sid = stream.cuda_stream
+    drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
+    u = torch.empty(n, dtype=torch.float64, device="cuda")
+    opts = cmg.options(seed=1412, precision="fp64")
+    ms = []
+    for k in range(5 + args.c1_steps):
+        flush.zero_()
+        e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+        e0.record(stream)
+        with cmg.Hierarchy(drp, dcol, dw, opts=opts, stream=sid) as h:
+            _, lam, st = h.fiedler(u_out=u, stream=sid)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= 5:
+            ms.append(e0.elapsed_time(e1))
+    uh = u.cpu().numpy()
+    ref_u, ref_lam, _, _, ref = oracle.fiedler(rp, col, w, seed=1412)
+    lam_exact = 2 - 2 * np.cos(np.pi / 64)
+    x = np.tile(np.arange(64), 64)
+    y = np.repeat(np.arange(64), 64)
+    Q = np.stack([np.cos(np.pi * (x + 0.5) / 64), np.cos(np.pi * (y + 0.5) / 64)], axis=1)
+    Q, _ = np.linalg.qr(Q)
+    srt = sorted(ms)
+    return {"workload": "grid2d_64x64_unit (n 4,096, nnz 16,128), FP64", "steps": len(ms),
+            "value": len(ms) / (sum(ms) / 1e3), "unit": UNIT,
+            "latency_ms": {"p50": srt[len(srt) // 2], "p99": srt[min(len(srt) - 1, int(0.99 * len(srt)))]},
+            "sweeps": st["sweeps"], "lambda2": lam, "residual": st["residual"],
+            "vs_oracle": {"vec_rel_err": _vec_err(uh, ref_u), "lambda2_rel_err": abs(lam - ref_lam) / ref_lam,
+                          "same_sweeps": st["sweeps"] == ref["sweeps"].tolist()},
+            "vs_closed_form": {"lambda2_exact": lam_exact, "lambda2_rel_err": (lam - lam_exact) / lam_exact,
+                               "fiedler_space_residual": float(np.linalg.norm(uh - Q @ (Q.T @ uh))),
+                               "note": "default (tolerance) mode is an approximation: lambda~ >= lambda2"}}
 
 
 BATCH_WORKLOAD = ("4096 graphs, n log-uniform [500, 20000], random geometric (mean degree 8) / "
@@ -531,9 +826,15 @@ def run_batch(args, stream, flush):
                 "angle_max": float(ang.max()), "angle_p99": float(np.percentile(ang, 99)),
                 "graphs_within_1e-6_and_1e-4": int(((rel <= 1e-6) & (ang <= 1e-4)).sum())}
 
-    res["fp32_vs_fp64_replay"] = compare(lam32, u32)
-    res["fp32_vs_fp64_replay"]["note"] = "FP32 sweeps with the FP64 run's per-graph, per-level sweep counts"
-    res["fp32_vs_fp64_tolerance_mode"] = compare(lam32_tol, u32_tol)
+    res["fp32_vs_gpu_fp64_replay"] = compare(lam32, u32)
+    res["fp32_vs_gpu_fp64_replay"]["note"] = ("FP32 sweeps with the GPU FP64 run's per-graph, per-level "
+                                              "sweep counts, every graph (accuracy_vs_oracle compares "
+                                              "with the CPU oracle)")
+    res["fp32_vs_gpu_fp64_tolerance_mode"] = compare(lam32_tol, u32_tol)
+    # arrays for the oracle comparison (removed before printing)
+    res["_graphs"], res["_union"] = graphs, (rp, col, w, offs)
+    res["_u64"], res["_lam64"], res["_sweeps64"] = u64, lam64, sweeps64
+    res["_u32_tol"], res["_lam32_tol"] = u32_tol, lam32_tol
     # the plain FP64 form: one graph at a time through cmg_setup / cmg_fiedler
     idx = list(range(0, G, max(1, G // args.batch_plain_sample)))
     torch.cuda.synchronize()
@@ -567,8 +868,11 @@ def run_chung_lu(args, stream, flush):
     drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
     u = torch.empty(n, dtype=torch.float64, device="cuda")
     deg = rp[1:] - rp[:-1]
+    d = np.add.reduceat(w, rp[:-1])
+    bound = n / (n - 1) * float(d.min())
     out = {"workload": cl_workload(args.cl_n), "n": n, "nnz": nnz, "max_degree": int(deg.max()),
-           "generate_s": round(gen_s, 1)}
+           "generate_s": round(gen_s, 1), "lambda2_upper_bound": bound,
+           "lambda2_upper_bound_note": "Fiedler: lambda2 <= n/(n-1) min_i d_i (weighted degree)"}
     res = {}
     for prec in ("fp32", "fp64"):
         opts = cmg.options(seed=1412, precision=prec, timing=1)
@@ -583,6 +887,7 @@ def run_chung_lu(args, stream, flush):
             e1.record(stream)
             e1.synchronize()
             kinds = h.level_kernels()
+            h_prec = h.level_precision()
             h.close()
             if k >= args.cl_warmup:
                 ms.append(e0.elapsed_time(e1))
@@ -590,6 +895,7 @@ def run_chung_lu(args, stream, flush):
         by0 = st["sweeps"][0] * ((8 if prec == "fp32" else 12) * st["nnz"][0] + (12 if prec == "fp32" else 20) * st["n"][0])
         res[prec] = {"u": u.cpu().numpy(), "lam": lam, "sweeps": st["sweeps"]}
         out[prec] = {"value": len(ms) / (sum(ms) / 1e3), "unit": "solves/s", "ms_per_step": statistics.mean(ms),
+                     "level_precision": h_prec,
                      "setup_ms": statistics.mean(setup), "levels": st["levels"], "sweeps": st["sweeps"],
                      "level_n": st["n"], "level_nnz": st["nnz"],
                      "level_kernel": [KERNEL_KIND[k] for k in kinds[0]], "level_staged": kinds[1],
@@ -606,6 +912,15 @@ def run_chung_lu(args, stream, flush):
     c = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
     out["fp32_vs_fp64_replay"] = {"lambda2_rel": abs(lam32 - res["fp64"]["lam"]) / abs(res["fp64"]["lam"]),
                                   "angle": float(np.arccos(min(1.0, c)))}
+    lam = res["fp64"]["lam"]
+    out["meets_lambda2_target"] = bool(lam <= bound * (1 + 1e-6))
+    out["accuracy_note"] = (
+        f"the returned Rayleigh quotient ({lam:.4g}) is {lam / bound:.0f} times Fiedler's upper bound "
+        f"on lambda2 ({bound:.4g}): with the paper's stop rule (cos >= 1 - 1e-8) the power iteration "
+        "ends once a sweep turns the vector by less than 1.4e-4 rad, which on this graph happens long "
+        "before the vector approaches the Fiedler vector (g / lambda2 >= 1e6); these solves/s are not "
+        "at the lambda2 <= 1e-6 target.  The same stop happens in the oracle (accuracy_vs_oracle."
+        "chung_lu_small)")
     c2 = abs(float(np.dot(res["fp32"]["u"], u64))) / (np.linalg.norm(res["fp32"]["u"]) * np.linalg.norm(u64))
     out["fp32_vs_fp64_tolerance_mode"] = {
         "lambda2_rel": abs(res["fp32"]["lam"] - res["fp64"]["lam"]) / abs(res["fp64"]["lam"]),
@@ -687,6 +1002,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cuda", choices=["cuda", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--c1-steps", type=int, default=50)
+    ap.add_argument("--no-oracle-checks", action="store_true")
+    ap.add_argument("--batch-oracle-sample", type=int, default=0,
+                    help="compare a seeded sample of this many batch graphs with the oracle (0: all)")
+    ap.add_argument("--cl-oracle-n", type=int, default=250_000,
+                    help="Chung-Lu vertices (before the largest component) of the oracle comparison (0: skip)")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--batch-graphs", type=int, default=4096)

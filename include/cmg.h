@@ -64,8 +64,8 @@ typedef enum cmg_status {
 enum { CMG_MEM_HOST = 0, CMG_MEM_DEVICE = 1 };
 /* Sweep precision.  FP64: every power-iteration sweep in FP64.  FP32_SWEEP:
  * the sweeps of the levels that carry the bytes run in FP32 with FP32
- * accumulation -- in cmg_setup / cmg_fiedler the levels of more than 65,536
- * rows, in the batched form union level 0 -- and every other level keeps
+ * accumulation -- in cmg_setup / cmg_fiedler the levels with at least 2^20
+ * stored entries, in the batched form union level 0 -- and every other level keeps
  * FP64 sweeps (those levels are latency-bound and run the longest sweep
  * chains, along which FP32 rounding would accumulate); in both forms the
  * stop statistic, mean and norm are float-float sums (about 48 bits), and

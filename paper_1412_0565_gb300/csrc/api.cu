@@ -219,8 +219,9 @@ cmg_status_t cmg::launch_to_float(long long m, const double *w, float *w32, cuda
     return launch_status();
 }
 
-// Fewest rows of a level that sweeps in FP32 in the FP32 form.
-constexpr int kFp32MinRows = 65536;
+// Fewest stored entries of a level that sweeps in FP32 in the FP32 form
+// (2^20 entries: at least 8 MB of FP32 sweep stream).
+constexpr long long kFp32MinEntries = 1ll << 20;
 
 static PiLevel level_view(const LevelData &L) {
     PiLevel v;
@@ -324,9 +325,10 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         if (st != CMG_OK) return st;
         level++;
     }
-    // ---- sweep precision per level.  In the FP32 form only levels of more
-    // than kFp32MinRows rows sweep in FP32: those carry the bytes that FP32
-    // halves.  Smaller levels keep FP64 sweeps: their sweeps are latency-bound
+    // ---- sweep precision per level.  In the FP32 form only levels with at
+    // least kFp32MinEntries stored entries sweep in FP32: those carry the
+    // bytes that FP32 halves.  Smaller levels keep FP64 sweeps: their sweeps
+    // are latency-bound
     // (FP32 saves little there), and they run the longest sweep chains
     // (thousands of sweeps on the coarse levels), along which FP32 rounding
     // accumulates in slowly converging components that the finer levels
@@ -340,7 +342,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         for (int k = 0; k < nlev; k++) {
             LevelData &L = h->lv[k];
             if (k == 0 && L.n <= 65536) CMG_TRY(sell_size(L.n, L.rp, cnt, &L.sell_nnz, s));
-            L.fp32 = (form32 && L.n > kFp32MinRows) ? 1 : 0;
+            L.fp32 = (form32 && L.nnz >= kFp32MinEntries) ? 1 : 0;
         }
     }
     for (auto &L : h->lv) {

@@ -153,7 +153,7 @@ def test_fp32_sweep_form_accuracy(name):
     prec = h.level_precision()
     h.close()
     assert st32["sweeps"] == ref["sweeps"].tolist()
-    assert all((p == "fp32") == (n > 65536) for p, n in zip(prec, st32["n"]))
+    assert all((p == "fp32") == (m >= 2**20) for p, m in zip(prec, st32["nnz"]))
     assert abs(lam32 - ref["lam"]) <= 1e-6 * abs(ref["lam"])
     assert angle(u32, ref["u"]) <= 1e-4
 
