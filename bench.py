@@ -479,6 +479,7 @@ def run_gpu(args):
     batch = run_batch(args, stream, flush) if (not args.no_batch and world == 1) else None
     serving = run_serving(args) if (not args.no_serving and world == 1) else None
     chung_lu = run_chung_lu(args, stream, flush) if (not args.no_chung_lu and world == 1) else None
+    gcmg = run_gcmg(args, stream) if (not args.no_gcmg and world == 1) else None
 
     if rank == 0:
         cpu = None
@@ -531,6 +532,7 @@ def run_gpu(args):
             "batch": batch,
             "serving": serving,
             "chung_lu": chung_lu,
+            "gcmg": gcmg,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -675,6 +677,53 @@ def oracle_checks(args, c2_graph, r64, r32, batch, chung_lu, stream):
 
 
 KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled"}
+
+TABLE4 = os.path.join(ROOT, "tests", "golden", "table4_gcmg.txt")
+
+
+def run_gcmg(args, stream):
+    """Alg. 4 (geometric CMG): the Table 4 setting (2D, N 1025, beta 4, k0 1,
+    coarsest 33 x 33) against the paper's printed errors and the oracle, and a
+    3D grid in the regime the paper calls optimal (4 < beta < 2^3)."""
+    import torch
+    import oracle
+    from paper_1412_0565_gb300 import cmg
+    sid = stream.cuda_stream
+    out = {}
+    for name, (dim, N, J, beta, k0, steps) in (("table4_2d", (2, 1025, 5, 4.0, 1, 20)),
+                                               ("grid3d", (3, 257, 5, 6.0, 1, 5))):
+        u = torch.empty(N ** dim, dtype=torch.float64, device="cuda")
+        ms = []
+        for k in range(2 + steps):
+            e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+            e0.record(stream)
+            _, r0, rk, ks = cmg.gcmg_grid(dim, N, J, beta=beta, k0=k0, u_out=u, stream=sid)
+            e1.record(stream)
+            e1.synchronize()
+            if k >= 2:
+                ms.append(e0.elapsed_time(e1))
+        lam = [2 - 2 * np.cos(np.pi / ((N - 1) // 2 ** j + 1)) for j in range(J + 1)]
+        n_j = [((N - 1) // 2 ** j + 1) ** dim for j in range(J + 1)]
+        rec = {"workload": f"unit grid graph {N}^{dim}, {J} geometric coarsenings, beta {beta}, k0 {k0}",
+               "value": len(ms) / (sum(ms) / 1e3), "unit": "solves/s", "ms": statistics.median(ms),
+               "k": ks.tolist(), "vertex_sweeps": int(sum(k_ * m for k_, m in zip(ks.tolist(), n_j))),
+               "err_r0": [abs(l - r) for l, r in zip(lam, r0)], "err_rk": [abs(l - r) for l, r in zip(lam, rk)]}
+        if dim * N ** dim <= 2_200_000 and not args.no_oracle_checks:
+            ref = oracle.gcmg_grid(dim, N, J, beta=beta, k0=k0)
+            uh = u.cpu().numpy()
+            rec["vs_oracle"] = {"rq_rel_err_max": float(max(np.max(np.abs(r0 - ref["r0"]) / ref["r0"]),
+                                                            np.max(np.abs(rk - ref["rk"]) / ref["rk"]))),
+                                "vec_rel_err": _vec_err(uh, ref["u"])}
+        if name == "table4_2d":
+            with open(TABLE4) as f:
+                rows = [l.split() for l in f if l.strip() and not l.startswith("#")]
+            rec["table4"] = {"paper_err_r0": [float(r[1]) for r in rows],
+                             "paper_err_rk": [float(r[2]) for r in rows],
+                             "max_rel_diff": max(max(abs(rec["err_r0"][int(r[0])] - float(r[1])) / float(r[1]),
+                                                     abs(rec["err_rk"][int(r[0])] - float(r[2])) / float(r[2]))
+                                                 for r in rows)}
+        out[name] = rec
+    return out
 
 
 def run_c1(args, stream, flush):
@@ -1005,6 +1054,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--no-gcmg", action="store_true")
     ap.add_argument("--c1-steps", type=int, default=50)
     ap.add_argument("--no-oracle-checks", action="store_true")
     ap.add_argument("--batch-oracle-sample", type=int, default=0,

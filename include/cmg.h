@@ -419,6 +419,33 @@ cmg_status_t cmg_server_get_stats(cmg_server_t s, cmg_server_stats_t *out);
 cmg_status_t cmg_server_destroy(cmg_server_t s);
 
 /* ------------------------------------------------------------------------
+ * Geometric cascadic multigrid, Alg. 4 (Sec. 3), in the structured setting of
+ * the paper's Table 4 experiment (Sec. 4): the unit-weight grid graph on
+ * N^dim vertices (dim 2: 5-point, dim 3: 7-point; vertex (x, y, z) has id
+ * (z N + y) N + x), coarsened geometrically J times by keeping every other
+ * vertex (level j has N_j = (N - 1)/2^j + 1 vertices per side; N - 1 must be
+ * a multiple of 2^J).  The coarsest level starts from its exact eigenvector
+ * for lambda_2 that varies along x, cos(pi (x + 1/2) / N_J) (Alg. 4 line 2:
+ * solved exactly); every finer level from the multilinear interpolant of the
+ * coarser result, made orthogonal to 1 and normalised, then k_j =
+ * ceil(k0 beta^j) smoothing steps u <- (I - A_j / ||A_j||_inf) u (Alg. 4
+ * line 4), each followed by Gram-Schmidt against 1 and normalisation.
+ *   u_out: double[N^dim] in `u_mem` memory, or NULL: the level-0 result.
+ *   r0_out, rk_out (host double[J+1], nullable): per level j the Rayleigh
+ *     quotient u^T A_j u / u^T u of the prolonged start and of the result
+ *     after the k_j steps (Table 4 prints |lambda_2^(j) - r0| and
+ *     |lambda_2^(j) - rk| with lambda_2^(j) = 2 - 2 cos(pi / N_j)); for the
+ *     coarsest level both are its exact vector's quotient.
+ *   k_out (host int32[J+1], nullable): k_j (0 on the coarsest level).
+ * FP64 throughout.  Errors: INVALID_ARG (dim not 2 or 3, N < 3, N - 1 not a
+ * multiple of 2^J, J outside 0..30, k0 < 0, beta <= 0, bad u_mem), TOO_LARGE
+ * (2 dim N^dim >= 2^31), OOM, CUDA, DEVICE_TIMEOUT.  Synchronises `stream`.
+ * ---------------------------------------------------------------------- */
+cmg_status_t cmg_gcmg_grid(int32_t dim, int32_t N, int32_t J, double beta, int32_t k0,
+                           double *u_out, int32_t u_mem, double *r0_out, double *rk_out,
+                           int32_t *k_out, void *stream);
+
+/* ------------------------------------------------------------------------
  * Step entry points.  Each runs one step of the method on DEVICE buffers in
  * the library's internal layout (row_ptr as int32[n+1]) on `stream`; they
  * exist so every step can be checked on its own.  Inputs are assumed to meet

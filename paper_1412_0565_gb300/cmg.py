@@ -42,7 +42,7 @@ EXPORTS = [
     "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
     "cmg_batch_free", "cmg_server_config_default", "cmg_server_create", "cmg_server_add_graph",
     "cmg_server_submit", "cmg_server_submit_ex", "cmg_solve_options_default", "cmg_fiedler_ex",
-    "cmg_server_wait", "cmg_server_wait_for", "cmg_server_get_stats",
+    "cmg_server_wait", "cmg_gcmg_grid", "cmg_server_wait_for", "cmg_server_get_stats",
     "cmg_server_destroy",
 ]
 
@@ -180,6 +180,7 @@ def load(build_if_stale: bool = True):
             "cmg_server_add_graph": (I32, [V, I64, V, V, V, P(I64)]),
             "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
             "cmg_level_precision": (I32, [V, V]),
+            "cmg_gcmg_grid": (I32, [I32, I32, I32, F64, I32, V, I32, V, V, V, V]),
             "cmg_server_submit_ex": (I32, [V, I64, P(SolveOptions), V, P(I64)]),
             "cmg_solve_options_default": (I32, [V, P(SolveOptions)]),
             "cmg_fiedler_ex": (I32, [V, P(SolveOptions), V, I32, P(F64), P(Stats), V]),
@@ -690,3 +691,19 @@ def debug_stall_barrier(launch: int, barrier: int = 0):
     """Test hook: the launch-th next multi-CTA cooperative launch holds its grid
     barrier number `barrier`, so its bounded waits run out (launch < 0: off)."""
     _check(load().cmg_debug_stall_barrier(int(launch), int(barrier)), "debug_stall_barrier")
+
+
+def gcmg_grid(dim: int, N: int, J: int, *, beta: float = 4.0, k0: int = 1, u_out=None, stream=None):
+    """cmg_gcmg_grid: Alg. 4 on the unit N^dim grid graph with J geometric
+    coarsenings.  Returns (u, r0[J+1], rk[J+1], k[J+1]); u is numpy (host) or
+    the given torch CUDA float64 tensor."""
+    if u_out is None:
+        u_out = np.empty(N ** dim, dtype=np.float64)
+    p_u, mem = _ptr(u_out)
+    r0 = np.zeros(J + 1)
+    rk = np.zeros(J + 1)
+    ks = np.zeros(J + 1, dtype=np.int32)
+    _check(load().cmg_gcmg_grid(int(dim), int(N), int(J), float(beta), int(k0), p_u, mem,
+                                C.c_void_p(r0.ctypes.data), C.c_void_p(rk.ctypes.data),
+                                C.c_void_p(ks.ctypes.data), _stream(stream)), "gcmg_grid")
+    return u_out, r0, rk, ks
