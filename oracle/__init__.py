@@ -91,6 +91,10 @@ def _load():
                                      C.c_int32, I64P, C.c_int64, C.c_int64, C.c_int32,
                                      C.c_double, C.c_int32, F64P, F64P, F64P, F64P, I64P, F64P,
                                      F64P, F64P]
+        lib.orc_solve_block.restype = C.c_int32
+        lib.orc_solve_block.argtypes = [C.c_void_p, C.c_int32, C.c_uint64, C.c_double, C.c_int32,
+                                        I64P, C.c_int64, C.c_int64, C.c_int32, C.c_double, F64P,
+                                        F64P, F64P, I64P]
         lib.orc_gcmg_grid.restype = C.c_int32
         lib.orc_gcmg_grid.argtypes = [C.c_int32, C.c_int64, C.c_int32, C.c_double, C.c_int32, F64P,
                                       F64P, I64P, F64P]
@@ -285,6 +289,30 @@ class Hierarchy:
             out["start"] = [ts[off[j]:off[j + 1]].copy() if j <= top else None for j in range(J + 1)]
             out["end"] = [te[off[j]:off[j + 1]].copy() if j <= top else None for j in range(J + 1)]
         return out
+
+
+def eigenpairs(h: "Hierarchy", k: int, *, seed=None, tol=1e-8, replay=None, max_sweeps=20000,
+               max_sweeps_coarsest=100000, converged=False, conv_rtol=1e-11):
+    """k eigenpairs by the cascade with block power iteration (the Remark
+    after Alg. 4) on hierarchy h.  Returns dict(U [k, n0], lam[k], res[k],
+    sweeps, capped)."""
+    J = h.levels - 1
+    n0 = h.sizes()[0]
+    rep = np.zeros(J + 1, dtype=np.int64)
+    if replay is not None:
+        rep[:] = np.asarray(replay, dtype=np.int64)[: J + 1]
+    U = np.empty((k, n0))
+    lam = np.empty(k)
+    res = np.empty(k)
+    sweeps = np.zeros(J + 1, dtype=np.int64)
+    st = _load().orc_solve_block(h._h, int(k), C.c_uint64(h.seed if seed is None else seed),
+                                 float(tol), 2 if replay is not None else 0, _p(rep, C.c_int64),
+                                 int(max_sweeps), int(max_sweeps_coarsest), 1 if converged else 0,
+                                 float(conv_rtol), _p(U, C.c_double), _p(lam, C.c_double),
+                                 _p(res, C.c_double), _p(sweeps, C.c_int64))
+    if st < 0:
+        raise ValueError("k must be between 1 and n_J - 1")
+    return {"U": U, "lam": lam, "res": res, "sweeps": sweeps, "capped": bool(st)}
 
 
 def fiedler(rp, col, w, *, seed=1412, tol=1e-8, coarse_size=25, **kw):

@@ -817,3 +817,151 @@ ORC_EXPORT int32_t orc_gcmg_grid(int32_t dim, int64_t N, int32_t J, double beta,
     free(y);
     return 0;
 }
+
+/* ------------------------------------------------------------------ */
+/* k eigenpairs (the Remark after Alg. 4): the cascade of Alg. 1 carries k
+ * vectors instead of one.  On the coarsest level k Gaussian vectors
+ * (vector i from randn keyed by seed + i, R4); on every level, after each
+ * power-iteration sweep (each vector multiplied by B_g), the vectors are
+ * orthogonalised -- modified Gram-Schmidt in their order, each first
+ * against 1 (R7) and then against the earlier ones, then normalised -- and
+ * after the last level each vector's Rayleigh quotient is computed.
+ * Readings:
+ *   K1 orthogonalisation after every sweep (as R7 does for 1), so the k
+ *      vectors span the dominant k-dimensional invariant subspace of B_g on
+ *      the complement of 1, i.e. tend to the eigenvectors of lambda_2 ..
+ *      lambda_{k+1} (orthogonal iteration); the prolonged vectors are
+ *      orthogonalised before the first sweep of their level;
+ *   K2 stopping: a level stops when every vector's cosine with its previous
+ *      iterate is at least 1 - tol (R6 for each vector); at least one sweep;
+ *   K3 the sign rule R11 is applied to each returned vector.
+ * X holds the k vectors of length n one after another (vector i at X + i n). */
+static double mgs(int64_t n, int32_t k, double *X)
+{
+    double min_nrm = 1e300;
+    for (int32_t i = 0; i < k; i++) {
+        double *xi = X + (size_t)i * (size_t)n;
+        double s = 0.0;
+        for (int64_t r = 0; r < n; r++) s += xi[r];
+        double mean = s / (double)n;
+        for (int64_t r = 0; r < n; r++) xi[r] -= mean;
+        for (int32_t j = 0; j < i; j++) {
+            const double *xj = X + (size_t)j * (size_t)n;
+            double d = 0.0;
+            for (int64_t r = 0; r < n; r++) d += xi[r] * xj[r];
+            for (int64_t r = 0; r < n; r++) xi[r] -= d * xj[r];
+        }
+        double q = 0.0;
+        for (int64_t r = 0; r < n; r++) q += xi[r] * xi[r];
+        double nrm = sqrt(q);
+        if (nrm < min_nrm) min_nrm = nrm;
+        if (nrm > 0.0)
+            for (int64_t r = 0; r < n; r++) xi[r] /= nrm;
+    }
+    return min_nrm;
+}
+
+/* Block power iteration on one level (K1, K2).  X: in the start vectors,
+ * out the result.  mode 0: tolerance rule (cap max_sweeps); mode 1: exactly
+ * k_fixed sweeps.  Returns the sweeps; *capped = 1 if the cap stopped it. */
+static int64_t block_power_iteration(int64_t n, const int64_t *rp, const int32_t *col,
+                                     const double *w, double g, int32_t k, double *X,
+                                     double tol, int32_t mode, int64_t k_fixed,
+                                     int64_t max_sweeps, int32_t *capped)
+{
+    double *d = (double *)malloc(sizeof(double) * (size_t)n);
+    double *V = (double *)malloc(sizeof(double) * (size_t)n * (size_t)k);
+    weighted_degrees(n, rp, w, d);
+    mgs(n, k, X);
+    int64_t s = 0;
+    if (capped) *capped = 0;
+    for (;;) {
+        if (mode == 1) {
+            if (s >= k_fixed) break;
+        } else if (s >= 1) {
+            /* every vector's cosine with its previous iterate (K2) */
+            int done = 1;
+            for (int32_t i = 0; i < k && done; i++)
+                if (!(cosine(n, X + (size_t)i * (size_t)n, V + (size_t)i * (size_t)n) >= 1.0 - tol))
+                    done = 0;
+            if (done) break;
+            if (s >= max_sweeps) {
+                if (capped) *capped = 1;
+                break;
+            }
+        }
+        memcpy(V, X, sizeof(double) * (size_t)n * (size_t)k);
+        for (int32_t i = 0; i < k; i++)
+            apply_bg(n, rp, col, w, d, g, V + (size_t)i * (size_t)n, X + (size_t)i * (size_t)n);
+        mgs(n, k, X);
+        s++;
+    }
+    free(d);
+    free(V);
+    return s;
+}
+
+/* Alg. 1 Steps 2-3 for k vectors on hierarchy h (schedule 0 tolerance, 2
+ * replay).  converged != 0: after level 0, sweep level 0 until every
+ * vector's residual ||(L - lambda_i I) u_i|| <= conv_rtol g_0 (test use).
+ * Outputs: U (k vectors of n_0, R11 sign each), lam[k], res[k] (Sec. 4 error
+ * metric per vector), sweeps[J+1].  Returns 1 if a cap was reached, 0, or -1
+ * when k is outside 1 .. n_J - 1.                                           */
+ORC_EXPORT int32_t orc_solve_block(orc_hierarchy *h, int32_t k, uint64_t seed, double tol,
+                                   int32_t schedule, const int64_t *replay, int64_t max_sweeps,
+                                   int64_t max_sweeps_coarsest, int32_t converged,
+                                   double conv_rtol, double *U, double *lam, double *res,
+                                   int64_t *sweeps_out)
+{
+    int32_t J = h->levels - 1;
+    if (k < 1 || (int64_t)k > h->lv[J].n - 1) return -1;
+    int32_t warn = 0, capped = 0;
+    orc_level *c = &h->lv[J];
+    double *Y = (double *)malloc(sizeof(double) * (size_t)c->n * (size_t)k);
+    for (int32_t i = 0; i < k; i++)
+        orc_gaussian_start(seed + (uint64_t)i, c->n, Y + (size_t)i * (size_t)c->n);
+    int32_t mode = (schedule == 2) ? 1 : 0;
+    c->sweeps = block_power_iteration(c->n, c->rp, c->col, c->w, c->g, k, Y, tol, mode,
+                                      mode ? replay[J] : 0, max_sweeps_coarsest, &capped);
+    warn |= capped;
+    for (int32_t j = J - 1; j >= 0; j--) {
+        orc_level *f = &h->lv[j];
+        int64_t nc = h->lv[j + 1].n;
+        double *X = (double *)malloc(sizeof(double) * (size_t)f->n * (size_t)k);
+        for (int32_t i = 0; i < k; i++)
+            for (int64_t r = 0; r < f->n; r++)
+                X[(size_t)i * (size_t)f->n + (size_t)r] = Y[(size_t)i * (size_t)nc + (size_t)f->agg[r]];
+        f->sweeps = block_power_iteration(f->n, f->rp, f->col, f->w, f->g, k, X, tol, mode,
+                                          mode ? replay[j] : 0, max_sweeps, &capped);
+        warn |= capped;
+        free(Y);
+        Y = X;
+    }
+    orc_level *f = &h->lv[0];
+    if (converged) {
+        for (int64_t it = 0; it < 100000; it++) {
+            double worst = 0.0;
+            for (int32_t i = 0; i < k; i++) {
+                double l, r;
+                orc_rayleigh_residual(f->n, f->rp, f->col, f->w, Y + (size_t)i * (size_t)f->n, &l, &r);
+                if (r > worst) worst = r;
+            }
+            if (worst <= conv_rtol * f->g) break;
+            block_power_iteration(f->n, f->rp, f->col, f->w, f->g, k, Y, tol, 1, 64, 64, NULL);
+        }
+    }
+    for (int32_t i = 0; i < k; i++) {
+        double *y = Y + (size_t)i * (size_t)f->n;
+        int64_t imax = 0;
+        for (int64_t r = 1; r < f->n; r++)
+            if (fabs(y[r]) > fabs(y[imax])) imax = r;
+        double sg = (y[imax] < 0.0) ? -1.0 : 1.0;
+        double *u = U + (size_t)i * (size_t)f->n;
+        for (int64_t r = 0; r < f->n; r++) u[r] = sg * y[r];
+        orc_rayleigh_residual(f->n, f->rp, f->col, f->w, u, lam + i, res + i);
+    }
+    for (int32_t j = 0; j <= J; j++)
+        if (sweeps_out) sweeps_out[j] = h->lv[j].sweeps;
+    free(Y);
+    return warn;
+}

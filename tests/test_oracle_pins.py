@@ -648,3 +648,85 @@ def test_gcmg_smoothing_improves_every_level(dim, N, J):
         lam = 2 - 2 * np.cos(np.pi / Nj)
         assert r["r0"][j] >= lam - 1e-15 and r["rk"][j] >= lam - 1e-15
         assert r["rk"][j] - lam <= r["r0"][j] - lam + 1e-18
+
+
+# ------------------------------------------------------------------ k eigenpairs (Remark after Alg. 4)
+def _conv_pairs(rp, col, w, k, seed=1412):
+    h = oracle.Hierarchy(rp, col, w, seed=seed)
+    r = oracle.eigenpairs(h, k, converged=True, conv_rtol=1e-14)
+    assert (r["res"] <= 1e-14 * oracle.gershgorin(rp, col, w)).all()
+    return r
+
+
+def test_eigenpairs_closed_form_path():
+    """Path P_n: lambda_j = 2 - 2 cos(pi (j-1)/n), eigenvectors
+    cos(pi (j-1)(x + 1/2)/n), all simple."""
+    n, k = 60, 4
+    rp, col, w = inputs.path(n)
+    r = _conv_pairs(rp, col, w, k)
+    x = np.arange(n)
+    for i in range(k):
+        m = i + 1
+        assert r["lam"][i] == pytest.approx(2 - 2 * np.cos(np.pi * m / n), rel=1e-12)
+        phi = np.cos(np.pi * m * (x + 0.5) / n)
+        phi /= np.linalg.norm(phi)
+        assert np.linalg.norm(align(r["U"][i], phi) - phi) <= 1e-9
+
+
+def test_eigenpairs_grid_with_double_eigenvalues():
+    """12 x 12 grid: lambda_2 = lambda_3 (x and y modes) and lambda_5 =
+    lambda_6; the first four returned vectors span the eigenspaces of
+    lambda_2..lambda_5 -- each cluster's vectors lie in its eigenspace."""
+    a = 12
+    rp, col, w = inputs.grid2d(a, a, "unit")
+    r = _conv_pairs(rp, col, w, 4)
+    L = dense_laplacian(rp, col, w)
+    ev, V = np.linalg.eigh(L)
+    assert np.allclose(r["lam"], ev[1:5], rtol=1e-12, atol=0)
+    # lambda_2 = lambda_3 and lambda_4 (= 2 - 2cos(pi/12) + 2 - 2cos(pi/12)) alone
+    assert subspace_residual(r["U"][0], V[:, 1:3]) <= 1e-9
+    assert subspace_residual(r["U"][1], V[:, 1:3]) <= 1e-9
+    assert subspace_residual(r["U"][2], V[:, 3:4]) <= 1e-9
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_eigenpairs_random_graphs_against_dense_eigensolver(seed):
+    n = [80, 140, 200][seed]
+    k = 3
+    rp, col, w = inputs.random_connected(n, 2 * n, seed=300 + seed)
+    ev, V = np.linalg.eigh(dense_laplacian(rp, col, w))
+    r = _conv_pairs(rp, col, w, k, seed=seed)
+    assert np.allclose(r["lam"], ev[1:k + 1], rtol=1e-12, atol=0)
+    for i in range(k):
+        gap = min(abs(ev[i + 1] - ev[i]), abs(ev[i + 2] - ev[i + 1]))
+        if gap > 1e-3 * ev[i + 1]:
+            assert np.linalg.norm(align(r["U"][i], V[:, i + 1]) - V[:, i + 1]) <= 1e-8
+
+
+def test_eigenpairs_default_mode_invariants():
+    """Default mode: orthonormal vectors orthogonal to 1 (Gram-Schmidt after
+    every sweep), canonical signs, and Courant-Fischer: the Rayleigh
+    quotients of an orthonormal k-frame bound the eigenvalues from above
+    (the i-th largest quotient >= lambda_{i+1}, by the min-max principle
+    applied to the frame's span)."""
+    rp, col, w = inputs.rgg(1200, 8.0, seed=7)
+    h = oracle.Hierarchy(rp, col, w)
+    r = oracle.eigenpairs(h, 4)
+    U = r["U"]
+    assert np.allclose(U @ U.T, np.eye(4), atol=1e-13)
+    assert np.abs(U.sum(axis=1)).max() <= 1e-12
+    for u in U:
+        assert u[np.argmax(np.abs(u))] > 0
+    ev = np.linalg.eigvalsh(dense_laplacian(rp, col, w))
+    assert (np.sort(r["lam"]) >= ev[1:5] - 1e-12).all()
+
+
+def test_one_eigenpair_is_the_fiedler_solve():
+    """With k = 1 the block cascade performs exactly the operations of the
+    single-vector cascade (same start, projection, stop rule)."""
+    rp, col, w = inputs.grid2d(40, 30, "uniform", seed=5)
+    h = oracle.Hierarchy(rp, col, w, seed=9)
+    a = h.solve()
+    b = oracle.eigenpairs(h, 1)
+    assert np.array_equal(a["sweeps"], b["sweeps"])
+    assert np.array_equal(a["u"], b["U"][0]) and a["lam"] == b["lam"][0]
