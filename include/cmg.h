@@ -193,6 +193,37 @@ cmg_status_t cmg_fiedler_ex(cmg_hierarchy_t h, const cmg_solve_options_t *so, do
                             int32_t u_mem, double *lambda2_out, cmg_stats_t *stats_out,
                             void *stream);
 
+/* Most eigenpairs cmg_eigenpairs computes at once. */
+#define CMG_MAX_EIGENPAIRS 16
+
+/*
+ * k approximate eigenpairs (lambda_2 .. lambda_{k+1} and their vectors) by
+ * the cascade of Alg. 1 with k vectors, the extension the Remark after
+ * Alg. 4 (Sec. 3) describes: k Gaussian vectors on the coarsest level
+ * (vector i keyed by seed + i), and on every level a block power iteration --
+ * each sweep multiplies the k vectors by B_g = g I - L and orthogonalises
+ * them (Gram-Schmidt against 1 and against the earlier vectors, in order,
+ * then normalisation) -- until every vector's cosine with its previous
+ * iterate is at least 1 - tol (or the hierarchy's FIXED / REPLAY schedule);
+ * then each vector's Rayleigh quotient.  The hierarchy's setup (and its
+ * options: tol, caps, schedule) is reused; sweeps are FP64.
+ *   k: 1 .. min(CMG_MAX_EIGENPAIRS, n_J - 1).
+ *   so: NULL for the hierarchy's seed; only so->seed is used (x0 must be NULL).
+ *   U_out: double[k * n_0] in `u_mem` memory, or NULL: vector i at
+ *     U_out + i n_0, unit length, orthogonal to 1 and to the others, scaled so
+ *     that its largest-magnitude entry (lowest index on ties) is positive.
+ *   lambda_out, residual_out (host double[k], nullable): per vector the
+ *     Rayleigh quotient u^T L u and ||(L - lambda I) u|| (Sec. 4).
+ *   stats_out (nullable): sizes and per-level sweeps (lambda2/residual: the
+ *     first vector's).
+ * Returns OK, WARN_MAXITER, or an error: INVALID_ARG, TOO_SMALL (the block
+ * lost rank: fewer than k independent directions), OOM, CUDA,
+ * DEVICE_TIMEOUT.  Synchronises `stream`.
+ */
+cmg_status_t cmg_eigenpairs(cmg_hierarchy_t h, int32_t k, const cmg_solve_options_t *so,
+                            double *U_out, int32_t u_mem, double *lambda_out, double *residual_out,
+                            cmg_stats_t *stats_out, void *stream);
+
 /* Level count and per-level sizes (host arrays of length >= levels, nullable). */
 cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_per_level,
                                 int64_t *nnz_per_level);

@@ -42,7 +42,7 @@ EXPORTS = [
     "cmg_batch_config", "cmg_batch_autotune", "cmg_batch_level_ms", "cmg_batch_device_bytes",
     "cmg_batch_free", "cmg_server_config_default", "cmg_server_create", "cmg_server_add_graph",
     "cmg_server_submit", "cmg_server_submit_ex", "cmg_solve_options_default", "cmg_fiedler_ex",
-    "cmg_server_wait", "cmg_gcmg_grid", "cmg_server_wait_for", "cmg_server_get_stats",
+    "cmg_server_wait", "cmg_gcmg_grid", "cmg_eigenpairs", "cmg_server_wait_for", "cmg_server_get_stats",
     "cmg_server_destroy",
 ]
 
@@ -181,6 +181,7 @@ def load(build_if_stale: bool = True):
             "cmg_server_submit": (I32, [V, I64, V, P(I64)]),
             "cmg_level_precision": (I32, [V, V]),
             "cmg_gcmg_grid": (I32, [I32, I32, I32, F64, I32, V, I32, V, V, V, V]),
+            "cmg_eigenpairs": (I32, [V, I32, V, V, I32, V, V, P(Stats), V]),
             "cmg_server_submit_ex": (I32, [V, I64, P(SolveOptions), V, P(I64)]),
             "cmg_solve_options_default": (I32, [V, P(SolveOptions)]),
             "cmg_fiedler_ex": (I32, [V, P(SolveOptions), V, I32, P(F64), P(Stats), V]),
@@ -332,6 +333,26 @@ class Hierarchy:
         _check(load().cmg_level_kernels(self._h, C.c_void_p(kind.ctypes.data),
                                         C.c_void_p(staged.ctypes.data)), "level_kernels")
         return kind.tolist(), staged.tolist()
+
+    def eigenpairs(self, k: int, *, seed=None, U_out=None, stream=None):
+        """cmg_eigenpairs: k approximate eigenpairs by the cascade with block
+        power iteration.  Returns (U [k, n] numpy or the given torch CUDA
+        tensor of k*n float64, lambda[k], residual[k], stats dict)."""
+        if U_out is None:
+            U_out = np.empty((k, self.n), dtype=np.float64)
+        p_u, mem = _ptr(U_out)
+        lam = np.zeros(k)
+        res = np.zeros(k)
+        stats = Stats()
+        so = None
+        if seed is not None:
+            so = SolveOptions()
+            _check(load().cmg_solve_options_default(self._h, C.byref(so)), "solve_options")
+            so.seed = int(seed)
+        _check(load().cmg_eigenpairs(self._h, int(k), C.byref(so) if so is not None else None, p_u, mem,
+                                     C.c_void_p(lam.ctypes.data), C.c_void_p(res.ctypes.data),
+                                     C.byref(stats), _stream(stream)), "cmg_eigenpairs")
+        return U_out, lam, res, stats.as_dict()
 
     def level_precision(self):
         """Per level: "fp32" or "fp64" sweeps."""

@@ -419,6 +419,22 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     return CMG_OK;
 }
 
+cmg_status_t cmg::hierarchy_view(cmg_hierarchy_t h, HierarchyView *out) {
+    if (!h || !out) return CMG_ERR_INVALID_ARG;
+    out->lv.clear();
+    for (const auto &L : h->lv) {
+        PiLevel v = level_view(L);
+        v.w32 = nullptr;
+        v.lay = nullptr;
+        out->lv.push_back(v);
+    }
+    out->device = h->device;
+    out->seed = h->opts.seed;
+    out->opts = h->opts;
+    out->gs = h->gs;
+    return CMG_OK;
+}
+
 // ------------------------------------------------------------------ C-ABI
 extern "C" {
 

@@ -233,6 +233,17 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s,
 // True when the shared-memory kernel can hold the whole level.
 bool small_level_fits(const PiLevel &lv, int fp32);
 
+// Read-only view of a resident hierarchy's levels (FP64 CSR, shifts, maps),
+// its device, its options' seed and its barrier state (api.cu).
+struct HierarchyView {
+    std::vector<PiLevel> lv;
+    int device;
+    uint64_t seed;
+    cmg_options_t opts;
+    GridSync *gs;
+};
+cmg_status_t hierarchy_view(cmg_hierarchy_t h, HierarchyView *out);
+
 cmg_status_t finalize(const PiLevel &lv, int fp32, void *const bufs[3], const PiResult *res,
                       double *u, int sign, int fresh, double *out2, GridSync *gs, cudaStream_t s,
                       const PiWorkspace *ws = nullptr);
