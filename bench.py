@@ -480,6 +480,7 @@ def run_gpu(args):
     serving = run_serving(args) if (not args.no_serving and world == 1) else None
     chung_lu = run_chung_lu(args, stream, flush) if (not args.no_chung_lu and world == 1) else None
     gcmg = run_gcmg(args, stream) if (not args.no_gcmg and world == 1) else None
+    study = run_schedule_study(args, stream) if (not args.no_study and world == 1) else None
 
     if rank == 0:
         cpu = None
@@ -533,6 +534,7 @@ def run_gpu(args):
             "serving": serving,
             "chung_lu": chung_lu,
             "gcmg": gcmg,
+            "schedule_study": study,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -723,6 +725,64 @@ def run_gcmg(args, stream):
                                                      abs(rec["err_rk"][int(r[0])] - float(r[2])) / float(r[2]))
                                                  for r in rows)}
         out[name] = rec
+    return out
+
+
+def run_schedule_study(args, stream):
+    """The fixed schedule k_j = ceil(k0 beta^j) of Sec. 3 (Theorem 3.10 and
+    its cost corollary) with the algebraic hierarchy, on unit-weight grids
+    whose lambda_2 is known in closed form: accuracy (relative error of the
+    returned Rayleigh quotient, residual) against cost (sum_j k_j n_j and
+    k_j nnz_j, device time) for a range of beta and k0, beside the paper's
+    tolerance rule.  With geometric coarsening (n_j / n_{j+1} = 2^d, h_{j+1}
+    / h_j = 2) the theory's window is 4 < beta < 2^d; heavy edge coarsening
+    shrinks a level about 3x, so the analogous window is
+    (n_j/n_{j+1})^(2/d) < beta < n_j/n_{j+1}, and the schedules tried stop
+    where the coarse levels' sweep counts explode (a configuration whose
+    predicted total exceeds the caps below is reported as skipped)."""
+    import torch
+    from paper_1412_0565_gb300 import cmg, inputs
+    sid = stream.cuda_stream
+    out = {}
+    for name, (graph, N) in (("grid2d_1024", (lambda: inputs.grid2d(1024, 1024, "unit"), 1024)),
+                              ("grid3d_100", (lambda: inputs.grid3d(100, 100, 100, "unit"), 100))):
+        rp, col, w = graph()
+        lam_exact = 2 - 2 * np.cos(np.pi / N)
+        drp, dcol, dw = (torch.from_numpy(a).cuda() for a in (rp, col, w))
+        u = torch.empty(len(rp) - 1, dtype=torch.float64, device="cuda")
+        rows = []
+        with cmg.Hierarchy(drp, dcol, dw, stream=sid, seed=1412) as h:
+            ns0 = h.sizes()[0]
+        ratio = float(np.exp(np.mean(np.log(np.array(ns0[:-2], float) / np.array(ns0[1:-1], float)))))
+        runs = [("tol", None, None)] + [("fixed", b, k0) for b in args.study_betas for k0 in args.study_k0s]
+        for sched, beta, k0 in runs:
+            if sched == "fixed":
+                kp = [int(np.ceil(k0 * beta ** j)) for j in range(len(ns0))]
+                if sum(kp) > 200_000 or sum(a * b for a, b in zip(kp, ns0)) > 300 * ns0[0]:
+                    rows.append({"schedule": sched, "beta": beta, "k0": k0, "skipped": True,
+                                 "predicted_sweeps": kp})
+                    continue
+            kw = dict(seed=1412, precision="fp64", timing=1)
+            if sched == "fixed":
+                kw.update(schedule="fixed", beta=float(beta), k0=int(k0))
+            with cmg.Hierarchy(drp, dcol, dw, stream=sid, **kw) as h:
+                ms = []
+                for rep in range(3):
+                    e0, e1 = (torch.cuda.Event(enable_timing=True) for _ in range(2))
+                    e0.record(stream)
+                    _, lam, st = h.fiedler(u_out=u, stream=sid)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+            ks, ns, nz = st["sweeps"], st["n"], st["nnz"]
+            rows.append({"schedule": sched, "beta": beta, "k0": k0, "sweeps": ks,
+                         "lambda2_rel_err": (lam - lam_exact) / lam_exact, "residual": st["residual"],
+                         "cost_kn": int(sum(a * b for a, b in zip(ks, ns))),
+                         "cost_knnz": int(sum(a * b for a, b in zip(ks, nz))),
+                         "solve_ms": min(ms)})
+        out[name] = {"n": len(rp) - 1, "lambda2_exact": lam_exact, "levels_n": ns0,
+                     "mean_coarsening_ratio": ratio,
+                     "window_beta": [ratio ** (2.0 / (2 if "2d" in name else 3)), ratio], "runs": rows}
     return out
 
 
@@ -1055,6 +1115,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-c1", action="store_true")
     ap.add_argument("--no-gcmg", action="store_true")
+    ap.add_argument("--no-study", action="store_true")
+    ap.add_argument("--study-betas", type=float, nargs="+", default=[1.5, 2.0, 2.5, 3.0, 3.5, 4.0])
+    ap.add_argument("--study-k0s", type=int, nargs="+", default=[1, 4, 16])
     ap.add_argument("--c1-steps", type=int, default=50)
     ap.add_argument("--no-oracle-checks", action="store_true")
     ap.add_argument("--batch-oracle-sample", type=int, default=0,
