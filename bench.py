@@ -832,7 +832,8 @@ def run_c1(args, stream, flush):
 BATCH_WORKLOAD = ("4096 graphs, n log-uniform [500, 20000], random geometric (mean degree 8) / "
                   "near-square 2D grid / Barabasi-Albert m=4 round-robin, U[0.5,1.5] weights, seed 1412")
 SERVE_WORKLOAD = ("requests drawn uniformly from {P} graphs with log n ~ Normal truncated to "
-                  "[ln 1e3, ln 2e6] (families and weights as the batch), Poisson arrivals")
+                  "[ln 1e3, ln 2e6] (families and weights as the batch), Poisson arrivals at rho x the "
+                  "closed-loop saturation rate")
 
 
 def _pool_workers():
@@ -1041,19 +1042,29 @@ KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled"}
 
 
 def run_serving(args):
-    """Request loop: closed-loop saturation, then Poisson arrivals at 0.8 of
-    it; FP32 server (batching, resident hierarchies) and plain FP64 server
-    (no batching) on the same request trace."""
+    """Config 5, the request loop: Poisson arrivals at rho x the closed-loop
+    saturation rate for each rho, on a trace of requests drawn from a pool of
+    graphs whose sizes are lognormal over 1e3 .. 2e6 vertices; FP32 server
+    (batching of cold small graphs, resident hierarchies) against a plain
+    FP64 server (no batching) at the same loads; p50/p99 latency, job mix,
+    device memory measured against the budget, and the FP32 results against
+    the CPU oracle on the served graphs small enough for it."""
     from paper_1412_0565_gb300 import cmg, inputs
     graphs = inputs.serving_graphs(args.serve_graphs, workers=_pool_workers())
     rng = np.random.default_rng(1412)
     trace = rng.integers(0, len(graphs), size=args.serve_requests)
-    out = {"workload": SERVE_WORKLOAD.format(P=len(graphs)), "requests": int(len(trace)),
-           "distinct_graphs": len(graphs), "n_max": int(max(len(g[0]) - 1 for g in graphs)),
-           "n_median": int(np.median([len(g[0]) - 1 for g in graphs]))}
-    lam_by = {}
-    for name, cfg, prec in (("fp32", dict(workers=4, max_batch=256, batch_max_n=50000), "fp32"),
-                            ("fp64_plain", dict(workers=4, max_batch=1), "fp64")):
+    sizes = [len(g[0]) - 1 for g in graphs]
+    out = {"workload": SERVE_WORKLOAD.format(P=len(graphs)), "requests_per_load": int(len(trace)),
+           "distinct_graphs": len(graphs), "distinct_in_trace": int(len(set(trace.tolist()))),
+           "n_max": int(max(sizes)), "n_median": int(np.median(sizes)),
+           "cut": (f"{len(trace)} requests per load from a pool of {len(graphs)} graphs (the configured "
+                   "10,000-request trace would take tens of minutes per load)"),
+           "min_batch": args.serve_min_batch}
+    servers = (("fp32", dict(workers=4, max_batch=256, batch_max_n=8192, min_batch=args.serve_min_batch),
+                "fp32", args.serve_rhos),
+               ("fp64_plain", dict(workers=4, max_batch=1), "fp64", [0.8]))
+    lam_served = {}
+    for name, cfg, prec, rhos in servers:
         def run(rate):
             with cmg.Server(seed=1412, precision=prec, **cfg) as srv:
                 ids = [srv.add_graph(*g) for g in graphs]
@@ -1074,33 +1085,79 @@ def run_serving(args):
 
         rs, dt, st = run(None)
         sat = len(trace) / dt
-        rs2, dt2, st2 = run(0.8 * sat)
-        lat = np.array([r["latency_ms"] for r in rs2])
-        lam_by[name] = np.array([r["lambda2"] for r in rs2])
-        out[name] = {"saturation_solves_s": sat, "rho": 0.8, "offered_rate": 0.8 * sat,
-                     "achieved_solves_s": len(trace) / dt2,
-                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "warm_fraction": float(np.mean([r["warm"] for r in rs2])),
-                     "batched_fraction": float(np.mean([r["batch_size"] > 1 for r in rs2])),
-                     "jobs": {k: st2[k] for k in ("single_jobs", "batch_jobs", "warm_jobs", "evictions")},
-                     "peak_device_bytes": st2["peak_bytes"]}
-    rel = np.abs(lam_by["fp32"] - lam_by["fp64_plain"]) / np.abs(lam_by["fp64_plain"])
-    out["fp32_vs_fp64_lambda2_rel"] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
-                                       "note": "tolerance mode (sweep counts may differ)"}
-    # precision alone on the serving graphs: FP32 sweeps replaying the FP64
-    # solve's per-level sweep counts
+        rec = {"saturation_solves_s": sat, "saturation_jobs": {k: st[k] for k in
+                                                              ("single_jobs", "batch_jobs", "warm_jobs")},
+               "loads": {}}
+        for rho in rhos:
+            rs2, dt2, st2 = run(rho * sat)
+            lat = np.array([r["latency_ms"] for r in rs2])
+            rec["loads"][str(rho)] = {
+                "offered_rate": rho * sat, "achieved_solves_s": len(trace) / dt2,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "warm_fraction": float(np.mean([r["warm"] for r in rs2])),
+                "batched_fraction": float(np.mean([r["batch_size"] > 1 for r in rs2])),
+                "jobs": {k: st2[k] for k in ("single_jobs", "batch_jobs", "warm_jobs", "evictions")},
+                "reserved_peak_bytes": st2["peak_bytes"], "measured_peak_bytes": st2["measured_peak_bytes"],
+                "budget_bytes": st2["budget_bytes"],
+                "within_budget": bool(st2["measured_peak_bytes"] <= st2["budget_bytes"])}
+            if rho == 0.8:
+                lam_served[name] = {int(k): r["lambda2"] for k, r in zip(trace, rs2)}
+        out[name] = rec
+    common = sorted(set(lam_served["fp32"]) & set(lam_served["fp64_plain"]))
+    rel = np.array([abs(lam_served["fp32"][k] - lam_served["fp64_plain"][k]) / abs(lam_served["fp64_plain"][k])
+                    for k in common])
+    out["fp32_vs_fp64_lambda2_rel_tolerance_mode"] = {"max": float(rel.max()), "p99": float(np.percentile(rel, 99)),
+                                                      "note": "each form stops on its own cosine test"}
+    # ---- a burst of small-graph requests (the batch's families and sizes,
+    # up to 8,192 vertices): Poisson arrivals far above one graph's solve
+    # rate, so cold requests pile up and the FP32 server batches them
+    idx = [i for i, nv in enumerate(inputs.batch_sizes(4096)) if nv <= 8192][:args.serve_burst_graphs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=_pool_workers(), mp_context=mp.get_context("spawn")) as ex:
+        small_g = list(ex.map(inputs.batch_graph, idx, chunksize=16))
+    burst = {"workload": (f"{len(small_g)} distinct graphs of the 4,096-graph batch's families with at "
+                          f"most 8,192 vertices, each requested once, Poisson arrivals at "
+                          f"{args.serve_burst_rate:.0f}/s")}
+    for name, cfg, prec in (("fp32_batched", dict(workers=4, max_batch=256, batch_max_n=8192, min_batch=32), "fp32"),
+                            ("fp64_plain", dict(workers=4, max_batch=1), "fp64")):
+        with cmg.Server(seed=1412, precision=prec, **cfg) as srv:
+            ids = [srv.add_graph(*g) for g in small_g]
+            arr = np.cumsum(np.random.default_rng(11).exponential(1.0 / args.serve_burst_rate, size=len(ids)))
+            t0 = time.perf_counter()
+            tickets = []
+            for gid, ta in zip(ids, arr):
+                d = t0 + ta - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets.append(srv.submit(gid, want_vector=False))
+            rs = [srv.wait(t)[1] for t in tickets]
+            dt = time.perf_counter() - t0
+            st = srv.stats()
+        lat = np.array([r["latency_ms"] for r in rs])
+        burst[name] = {"solves_s": len(rs) / dt, "p50_ms": float(np.percentile(lat, 50)),
+                       "p99_ms": float(np.percentile(lat, 99)),
+                       "batched_fraction": float(np.mean([r["batch_size"] > 1 for r in rs])),
+                       "jobs": {k: st[k] for k in ("single_jobs", "batch_jobs", "warm_jobs")},
+                       "measured_peak_bytes": st["measured_peak_bytes"]}
+    burst["fp32_batched_over_fp64_plain"] = burst["fp32_batched"]["solves_s"] / burst["fp64_plain"]["solves_s"]
+    out["small_graph_burst"] = burst
+    # precision alone against the oracle: the served graphs up to 50,000
+    # vertices, FP32 sweeps replaying the oracle's per-level sweep counts
+    import oracle
+    small = [i for i in sorted(set(trace.tolist())) if sizes[i] <= 50_000][:args.serve_oracle_sample]
     lam_rel, ang = [], []
-    for g in graphs[:args.serve_replay_sample]:
-        u64, l64, st64 = cmg.fiedler(*g, seed=1412, precision="fp64")
+    for i in small:
+        g = graphs[i]
+        ref = oracle.Hierarchy(*g, seed=1412).solve()
         u32, l32, _ = cmg.fiedler(*g, seed=1412, precision="fp32", schedule="replay",
-                                  replay_sweeps=st64["sweeps"])
-        lam_rel.append(abs(l32 - l64) / abs(l64))
-        c = abs(float(np.dot(u32, u64))) / (np.linalg.norm(u32) * np.linalg.norm(u64))
-        ang.append(float(np.arccos(min(1.0, c))))
-    out["fp32_vs_fp64_replay"] = {"graphs": len(lam_rel), "lambda2_rel_max": max(lam_rel),
-                                  "angle_max": max(ang),
-                                  "within_1e-6_and_1e-4": int(sum((r <= 1e-6) and (a <= 1e-4)
-                                                                  for r, a in zip(lam_rel, ang)))}
+                                  replay_sweeps=ref["sweeps"].tolist())
+        lam_rel.append(abs(l32 - ref["lam"]) / abs(ref["lam"]))
+        ang.append(_angle(u32, ref["u"]))
+    out["fp32_replay_vs_oracle"] = {"graphs": len(lam_rel), "lambda2_rel_err_max": max(lam_rel),
+                                    "angle_max": max(ang), "gate": "lambda2 <= 1e-6, angle <= 1e-4",
+                                    "within_gate": int(sum((r <= 1e-6) and (a <= 1e-4)
+                                                           for r, a in zip(lam_rel, ang)))}
     return out
 
 
@@ -1129,9 +1186,13 @@ def main():
     ap.add_argument("--batch-graphs", type=int, default=4096)
     ap.add_argument("--batch-steps", type=int, default=2)
     ap.add_argument("--batch-plain-sample", type=int, default=32)
-    ap.add_argument("--serve-graphs", type=int, default=48)
-    ap.add_argument("--serve-requests", type=int, default=160)
-    ap.add_argument("--serve-replay-sample", type=int, default=16)
+    ap.add_argument("--serve-graphs", type=int, default=96)
+    ap.add_argument("--serve-requests", type=int, default=240)
+    ap.add_argument("--serve-rhos", type=float, nargs="+", default=[0.5, 0.8, 0.95])
+    ap.add_argument("--serve-min-batch", type=int, default=8)
+    ap.add_argument("--serve-oracle-sample", type=int, default=24)
+    ap.add_argument("--serve-burst-graphs", type=int, default=1024)
+    ap.add_argument("--serve-burst-rate", type=float, default=4000.0)
     ap.add_argument("--no-chung-lu", action="store_true")
     ap.add_argument("--cl-steps", type=int, default=3)
     ap.add_argument("--cl-warmup", type=int, default=1)

@@ -384,13 +384,18 @@ cmg_status_t cmg_batch_free(cmg_batch_t b);
  * arriving while others run are admitted together as soon as a worker and
  * memory free up.  Pending requests are
  * taken first-fit in arrival order.  All requests use the server's options.
+ * Admission estimate: cmg_estimate_device_bytes, plus three more copies of
+ * level 0's stored levels for a graph whose largest degree exceeds 8 times
+ * its mean (the coarse levels of such heavy-tailed graphs stay dense).
  * ---------------------------------------------------------------------- */
 typedef struct cmg_server_s *cmg_server_t;
 
 typedef struct cmg_server_config {
     int32_t workers;       /* concurrent jobs, 1..64 (4)                              */
     int32_t max_batch;     /* graphs per batched job; 1 disables batching (256)       */
-    int64_t batch_max_n;   /* graphs with n <= batch_max_n are batched (50000)        */
+    int64_t batch_max_n;   /* graphs with n <= batch_max_n are batched (8192): a
+                              batched job runs each graph's sweeps on one thread
+                              group, so a larger graph is faster alone              */
     uint64_t mem_budget;   /* device bytes for jobs and resident hierarchies;
                               0 = 80% of the free device memory at creation          */
     int32_t keep_resident; /* keep single-form hierarchies after their solve (1)      */
@@ -411,12 +416,16 @@ typedef struct cmg_request {
 
 typedef struct cmg_server_stats {
     int64_t completed, single_jobs, batch_jobs, warm_jobs, evictions, resident;
-    uint64_t peak_bytes;   /* most device bytes reserved at once                     */
+    uint64_t peak_bytes;   /* most device bytes reserved at once (bookkeeping)       */
     uint64_t used_bytes;   /* reserved now (running jobs + resident hierarchies)     */
     uint64_t budget_bytes;
+    uint64_t measured_peak_bytes; /* most bytes of the library's device memory pool
+                              in use at once since cmg_server_create, as the CUDA
+                              driver counts them (the pool serves every user of the
+                              library on this device in this process)            */
 } cmg_server_stats_t;
 
-/* workers 4, max_batch 256, batch_max_n 50000, mem_budget 0, keep_resident 1,
+/* workers 4, max_batch 256, batch_max_n 8192, mem_budget 0, keep_resident 1,
  * min_batch 32. */
 cmg_status_t cmg_server_config_default(cmg_server_config_t *cfg);
 /* Starts the workers on the current device.  opts: NULL = defaults

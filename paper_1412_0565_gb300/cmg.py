@@ -118,7 +118,8 @@ class Request(C.Structure):
 class ServerStats(C.Structure):
     _fields_ = [("completed", C.c_int64), ("single_jobs", C.c_int64), ("batch_jobs", C.c_int64),
                 ("warm_jobs", C.c_int64), ("evictions", C.c_int64), ("resident", C.c_int64),
-                ("peak_bytes", C.c_uint64), ("used_bytes", C.c_uint64), ("budget_bytes", C.c_uint64)]
+                ("peak_bytes", C.c_uint64), ("used_bytes", C.c_uint64), ("budget_bytes", C.c_uint64),
+                ("measured_peak_bytes", C.c_uint64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -553,7 +554,7 @@ class Server:
     """Request loop for Fiedler solves (cmg_server_*): register host graphs,
     submit requests, wait for results.  Graph arrays are kept alive here."""
 
-    def __init__(self, *, workers=4, max_batch=256, batch_max_n=50000, mem_budget=0,
+    def __init__(self, *, workers=4, max_batch=256, batch_max_n=8192, mem_budget=0,
                  keep_resident=1, min_batch=32, opts: Options | None = None, **kw):
         lib = load()
         cfg = ServerConfig()

@@ -46,6 +46,10 @@ cmg_status_t dev_alloc(void **p, size_t bytes, cudaStream_t s);
 void dev_free(void *p, cudaStream_t s);
 // Test hook: make the k-th next allocation fail with CMG_ERR_OOM (k < 0: off).
 void debug_fail_alloc_after(long long k);
+// Most bytes of the current device's pool in use at once since the last
+// reset (a measurement of the driver's, not the library's bookkeeping);
+// reset != 0 restarts it from the bytes in use now.
+cmg_status_t pool_used_high(size_t *high, int reset);
 
 template <typename T>
 cmg_status_t dev_alloc_n(T **p, size_t count, cudaStream_t s) {

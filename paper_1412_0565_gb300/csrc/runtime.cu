@@ -99,6 +99,21 @@ void dev_free(void *p, cudaStream_t s) {
 
 void debug_fail_alloc_after(long long k) { g_fail_after.store(k); }
 
+cmg_status_t pool_used_high(size_t *high, int reset) {
+    int dev = 0;
+    CMG_CUDA(cudaGetDevice(&dev));
+    cudaMemPool_t pool;
+    CMG_TRY(pool_for(dev, &pool));
+    if (reset) {
+        uint64_t zero = 0;
+        CMG_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &zero));
+    }
+    uint64_t v = 0;
+    CMG_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemHigh, &v));
+    if (high) *high = (size_t)v;
+    return CMG_OK;
+}
+
 cmg_status_t device_info(DeviceInfo *out) {
     int dev = 0;
     CMG_CUDA(cudaGetDevice(&dev));

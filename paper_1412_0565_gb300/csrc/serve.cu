@@ -44,6 +44,7 @@ uint64_t now_ns() {
 
 struct Graph {
     int64_t n = 0, nnz = 0;
+    bool heavy_tail = false;      // max degree > 8 x mean: coarse levels stay dense
     const int64_t *rp = nullptr;
     const int32_t *col = nullptr;
     const double *w = nullptr;
@@ -98,6 +99,14 @@ namespace {
 size_t estimate(const cmg_server_s *S, const Graph &g) {
     size_t b = 0;
     cmg_estimate_device_bytes(g.n, g.nnz, S->opts.precision, &b);
+    if (g.heavy_tail) {
+        // the coarse levels of a heavy-tailed graph keep most of level 0's
+        // entries (a 4.19M-vertex Chung-Lu graph: 4x level 0 over all levels),
+        // where the general estimate budgets one more copy of level 0: add
+        // three more copies of level 0's stored levels
+        const double wb = (S->opts.precision == CMG_PRECISION_FP32_SWEEP) ? 16.0 : 12.0;
+        b += (size_t)(3.0 * (wb * (double)g.nnz + 16.0 * (double)g.n));
+    }
     return b;
 }
 
@@ -340,7 +349,7 @@ extern "C" cmg_status_t cmg_server_config_default(cmg_server_config_t *cfg) {
     memset(cfg, 0, sizeof(*cfg));
     cfg->workers = 4;
     cfg->max_batch = 256;
-    cfg->batch_max_n = 50000;
+    cfg->batch_max_n = 8192;
     cfg->mem_budget = 0;
     cfg->keep_resident = 1;
     cfg->min_batch = 32;
@@ -385,6 +394,9 @@ extern "C" cmg_status_t cmg_server_create(const cmg_server_config_t *cfg, const 
         }
         S->streams.push_back(st);
     }
+    // the measured high-water mark starts here (the pool is the library's,
+    // shared by every user of the library in this process on this device)
+    cmg::pool_used_high(nullptr, 1);
     for (int k = 0; k < c.workers; k++) S->workers.emplace_back(worker_main, S, S->streams[k], k);
     *out = S;
     return CMG_OK;
@@ -396,10 +408,13 @@ extern "C" cmg_status_t cmg_server_add_graph(cmg_server_t S, int64_t n, const in
     if (n < 2) return CMG_ERR_TOO_SMALL;
     const int64_t nnz = row_ptr[n];
     if (nnz < 0 || (nnz > 0 && (!col || !w))) return CMG_ERR_INVALID_ARG;
+    int64_t maxdeg = 0;
+    for (int64_t i = 0; i < n; i++) maxdeg = std::max<int64_t>(maxdeg, row_ptr[i + 1] - row_ptr[i]);
     std::lock_guard<std::mutex> lk(S->mu);
     Graph g;
     g.n = n;
     g.nnz = nnz;
+    g.heavy_tail = (double)maxdeg > 8.0 * (double)nnz / (double)n;
     g.rp = row_ptr;
     g.col = col;
     g.w = w;
@@ -486,6 +501,14 @@ extern "C" cmg_status_t cmg_server_get_stats(cmg_server_t S, cmg_server_stats_t 
     *out = S->stats;
     out->peak_bytes = S->peak;
     out->used_bytes = S->used;
+    {
+        int prev = 0;
+        cudaGetDevice(&prev);
+        if (prev != S->device) cudaSetDevice(S->device);
+        size_t hi = 0;
+        if (cmg::pool_used_high(&hi, 0) == CMG_OK) out->measured_peak_bytes = hi;
+        if (prev != S->device) cudaSetDevice(prev);
+    }
     out->budget_bytes = S->budget;
     int64_t res = 0;
     for (auto &g : S->graphs) res += g.h ? 1 : 0;

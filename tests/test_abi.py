@@ -124,4 +124,5 @@ def test_public_structs_match_header_sizes():
     assert C.sizeof(cmg.BatchShape) == 16
     assert C.sizeof(cmg.ServerConfig) == 4 + 4 + 8 + 8 + 4 + 4
     assert C.sizeof(cmg.Request) == 16 + 16 + 24
-    assert C.sizeof(cmg.ServerStats) == 6 * 8 + 3 * 8
+    assert C.sizeof(cmg.ServerStats) == 6 * 8 + 4 * 8
+    assert C.sizeof(cmg.SolveOptions) == 8 + 8 + 4 + 4 + 4 * 4
