@@ -141,6 +141,12 @@ __device__ __forceinline__ double start_value(const PiArgs &a, int i, const void
 // memory.  Slot for sweep t holds what the rows of sweep t need (m_{t-1},
 // e_{t-1}) and the stop decision taken for sweep t-2.
 struct Slot {
+    // FP64 rows: the same scalars as doubles, formed once per sweep by the
+    // control warp (an FP64 operation issues at 2 per SM per clock: per-row-
+    // thread copies of this arithmetic cost every row warp FP64 issue slots)
+    double m_d;     // m as a double
+    double sig_d;   // 2^e / g
+    double gm_d;    // g m
     ff m;           // mean estimate to subtract
     int e;          // power-of-two rescale exponent
     int stop;       // decision for sweep t-2: 0 continue, 1 stop
@@ -148,13 +154,20 @@ struct Slot {
     int pad;
 };
 
-__device__ __forceinline__ Slot slot_make(ff m, int e) {
+// fp64: also form the doubles (the FP32 kernels leave them unused)
+__device__ __forceinline__ Slot slot_make(ff m, int e, double g, bool fp64) {
     Slot sl;
     sl.m = m;
     sl.e = e;
     sl.stop = 0;
     sl.zero = 0;
     sl.pad = 0;
+    sl.m_d = sl.sig_d = sl.gm_d = 0.0;
+    if (fp64) {
+        sl.m_d = ff_to_double(m);
+        sl.sig_d = ldexp(1.0 / g, e);
+        sl.gm_d = g * sl.m_d;
+    }
     return sl;
 }
 
@@ -175,7 +188,7 @@ struct Ctl {
 // and fills the slot for sweep s+2 (m_{s+1}, e_{s+1}).  `count_exit`: the
 // loop ends after sweep s regardless (fixed count or sweep cap reached).
 __device__ __forceinline__ void ctrl_step(const PiArgs &a, int s, const Part &P, Ctl &c,
-                                          Slot *next, bool count_exit) {
+                                          Slot *next, bool count_exit, bool fp64) {
     const float nf = (float)a.n;
     // the mean is at rounding level: n mu^2 and n mu mu_prev need no extra
     // precision, mu itself does (it is subtracted from the iterate)
@@ -217,7 +230,7 @@ __device__ __forceinline__ void ctrl_step(const PiArgs &a, int s, const Part &P,
         if (l2 < -24.f) e_next = (int)(-l2);
     }
     if (next) {
-        *next = slot_make(m_next, e_next);
+        *next = slot_make(m_next, e_next, a.g, fp64);
         next->stop = stop ? 1 : 0;
         next->zero = zero ? 1 : 0;
     }
@@ -376,8 +389,8 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
         const int e0 = start_exponent(ss0);
         ctl_init(c, a, mu0, ss0, e0);
         if (lane == 0) {
-            s_slot[1] = slot_make(ff_from_double(mu0), e0);  // sweep 1: exact mean of y_0
-            s_slot[0] = slot_make(ff_zero(), 0);             // sweep 2: m_1 = 0
+            s_slot[1] = slot_make(ff_from_double(mu0), e0, a.g, fp64);  // sweep 1: exact mean of y_0
+            s_slot[0] = slot_make(ff_zero(), 0, a.g, fp64);             // sweep 2: m_1 = 0
         }
     }
     __syncthreads();
@@ -412,15 +425,15 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
                 }
                 q = warp_sum_part(q);
                 Slot nx;
-                ctrl_step(a, s, q, c, &nx, false);
+                ctrl_step(a, s, q, c, &nx, false, fp64);
                 if (lane == 0) s_slot[s & 1] = nx;
             }
         } else {
             // ---- rows of sweep s+1
             const int rt = tid - 32;
-            const T m = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
-            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
-            const T gm = g * m;
+            const T m = fp64 ? (T)sl.m_d : (T)sl.m.hi;
+            const T sig = fp64 ? (T)sl.sig_d : (T)scale2f(inv_gf, sl.e);
+            const T gm = fp64 ? (T)sl.gm_d : g * m;
             Acc<T> acc;
             acc.reset();
             for (int t = tb; t < te; t++) {
@@ -540,7 +553,7 @@ __global__ void __launch_bounds__(kTileThreads, 2) k_power_tiled(PiArgs a, GridS
                 q = part_add(q, t);
             }
             q = warp_sum_part(q);
-            ctrl_step(a, s, q, c, nullptr, true);
+            ctrl_step(a, s, q, c, nullptr, true, fp64);
         }
         if (blockIdx.x == 0 && lane == 0) {
             const int rs = c.res_sweep;
@@ -660,8 +673,8 @@ __global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 
         const int e0 = start_exponent(ss0);
         ctl_init(c, a, mu0, ss0, e0);
         if (lane == 0) {
-            s_slot[1] = slot_make(ff_from_double(mu0), e0);
-            s_slot[0] = slot_make(ff_zero(), 0);
+            s_slot[1] = slot_make(ff_from_double(mu0), e0, a.g, fp64);
+            s_slot[0] = slot_make(ff_zero(), 0, a.g, fp64);
         }
     }
     __syncthreads();
@@ -699,13 +712,13 @@ __global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 
                 }
                 q = warp_sum_part(q);
                 Slot nx;
-                ctrl_step(a, s, q, c, &nx, false);
+                ctrl_step(a, s, q, c, &nx, false, fp64);
                 if (lane == 0) s_slot[s & 1] = nx;
             }
         } else {
-            const T m = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
-            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
-            const T gm = g * m;
+            const T m = fp64 ? (T)sl.m_d : (T)sl.m.hi;
+            const T sig = fp64 ? (T)sl.sig_d : (T)scale2f(inv_gf, sl.e);
+            const T gm = fp64 ? (T)sl.gm_d : g * m;
             Acc<T> acc;
             acc.reset();
             auto finish = [&](int i, T xi, T ac) {
@@ -819,7 +832,7 @@ __global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 
                 q = part_add(q, t);
             }
             q = warp_sum_part(q);
-            ctrl_step(a, s, q, c, nullptr, true);
+            ctrl_step(a, s, q, c, nullptr, true, fp64);
         }
         if (blockIdx.x == 0 && lane == 0) {
             const int rs = c.res_sweep;
@@ -855,10 +868,37 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     int *s_rp = reinterpret_cast<int *>(s_w + E);
     int *s_col = s_rp + n + 1;
     int *s_soff = s_col + E;
+    // FP64 form: every row thread's stop sums (A, B, C as doubles), by sweep
+    // parity; the control warp reduces them (one float-float conversion per
+    // control lane, instead of one per row thread: conversions issue on the
+    // FP64 pipe)
+    double *s_dacc = reinterpret_cast<double *>(
+        (reinterpret_cast<uintptr_t>(s_soff + (n / 32 + 2)) + 7) & ~(uintptr_t)7);
     __shared__ Part s_pw[2][32];
     __shared__ Slot s_slot[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nw = blockDim.x >> 5;
+    // the control warp's sums of the row warps' partials of parity `par`, in
+    // a fixed order (rows warps in order per lane, then the lanes' xor tree)
+    auto ctl_part = [&](int par) -> Part {
+        if constexpr (sizeof(T) == 8) {
+            double A = 0.0, B = 0.0, C = 0.0;
+            for (int w = 1; w < nw; w++) {
+                const double *src = s_dacc + ((size_t)par * blockDim.x + 32 * w + lane) * 3;
+                A += src[0];
+                B += src[1];
+                C += src[2];
+            }
+            Part p;
+            p.A = ff_from_double(A);
+            p.B = ff_from_double(B);
+            p.C = ff_from_double(C);
+            return warp_sum_part(p);
+        } else {
+            const Part q = (lane >= 1 && lane < nw) ? s_pw[par][lane] : part_zero();
+            return warp_sum_part(q, 1, pow2_at_least(nw));
+        }
+    };
     const T *__restrict__ wv = wsel<T>(a);
     const T g = (T)a.g;
     const float inv_gf = 1.0f / (float)a.g;
@@ -935,8 +975,8 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
         const int e0 = start_exponent(ss0);
         ctl_init(c, a, mu0, ss0, e0);
         if (lane == 0) {
-            s_slot[1] = slot_make(ff_from_double(mu0), e0);
-            s_slot[0] = slot_make(ff_zero(), 0);
+            s_slot[1] = slot_make(ff_from_double(mu0), e0, a.g, fp64);
+            s_slot[0] = slot_make(ff_zero(), 0, a.g, fp64);
         }
     }
     __syncthreads();
@@ -962,18 +1002,17 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
         if (warp == 0) {
             if (lane == 0) TRACE(s, 0);
             if (s >= 1) {
-                Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
-                q = warp_sum_part(q, 1, pow2_at_least(nw));
+                const Part q = ctl_part(s & 1);
                 Slot nx;
-                ctrl_step(a, s, q, c, &nx, false);
+                ctrl_step(a, s, q, c, &nx, false, fp64);
                 if (lane == 0) s_slot[s & 1] = nx;
             }
             if (lane == 0) TRACE(s, 1);
         } else {
             if (lane == 0 && warp == 1) TRACE(s, 4);
-            const T mT = fp64 ? (T)ff_to_double(sl.m) : (T)sl.m.hi;
-            const T sig = fp64 ? (T)ldexp(inv_gd, sl.e) : (T)scale2f(inv_gf, sl.e);
-            const T gm = g * mT;
+            const T mT = fp64 ? (T)sl.m_d : (T)sl.m.hi;
+            const T sig = fp64 ? (T)sl.sig_d : (T)scale2f(inv_gf, sl.e);
+            const T gm = fp64 ? (T)sl.gm_d : g * mT;
             Acc<T> acc;
             acc.reset();
             for (int base = rt / G;; base += groups) {
@@ -1048,8 +1087,15 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
                 if (lane == 0 && warp == 1) TRACE(s, 6);
             }
             // only the lanes leading a row group hold sums
-            Part p = warp_sum_part(acc.get(), G);
-            if (lane == 0) s_pw[(s + 1) & 1][warp] = p;
+            if constexpr (sizeof(T) == 8) {
+                double *dst = s_dacc + ((size_t)((s + 1) & 1) * blockDim.x + tid) * 3;
+                dst[0] = acc.A;
+                dst[1] = acc.B;
+                dst[2] = acc.C;
+            } else {
+                const Part p = warp_sum_part(acc.get(), G);
+                if (lane == 0) s_pw[(s + 1) & 1][warp] = p;
+            }
             if (lane == 0 && warp == 1) TRACE(s, 2);
             if (lane == 0 && warp == nw - 1) TRACE(s, 3);
         }
@@ -1059,9 +1105,8 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     __shared__ int s_rb, s_rbp;
     if (warp == 0) {
         if (exit_kind == 2 && !no_sweeps) {
-            Part q = (lane >= 1 && lane < nw) ? s_pw[s & 1][lane] : part_zero();
-            q = warp_sum_part(q, 1, pow2_at_least(nw));
-            ctrl_step(a, s, q, c, nullptr, true);
+            const Part q = ctl_part(s & 1);
+            ctrl_step(a, s, q, c, nullptr, true, fp64);
         }
         if (lane == 0) {
             const int rs = c.res_sweep;
@@ -1180,7 +1225,9 @@ static long long small_entries(const PiLevel &lv, int G) {
 
 static size_t small_bytes(const PiLevel &lv, int G, int fp32) {
     const long long e = small_entries(lv, G);
-    return fp32 ? small_smem_bytes<float>(lv.n, e) : small_smem_bytes<double>(lv.n, e);
+    if (fp32) return small_smem_bytes<float>(lv.n, e);
+    // plus the row threads' FP64 stop sums: 2 parities x 3 doubles per thread
+    return small_smem_bytes<double>(lv.n, e) + 8 + 48 * (size_t)small_threads(lv.n, G);
 }
 
 int stage_capacity(int fp32) {
