@@ -232,11 +232,17 @@ cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_p
  * nullable).  kind_out[j]: 0 = one CTA with the level in shared memory,
  * 1 = slice kernel over the level's sweep layout, 2 = the same with the
  * iterate's first staged_out[j] entries (its highest-degree rows) copied to
- * shared memory every sweep, 3 = row-tile kernel.  Staging is chosen at setup
- * where the gathers it serves are several per staged entry and SM; the
- * environment variable CMG_STAGE=0 (never) or CMG_STAGE=1 (every slice
- * level), read by cmg_setup, overrides that.  Results do not depend on the
- * kernel.  Errors: INVALID_ARG if h is NULL. */
+ * shared memory every sweep, 3 = row-tile kernel, 4 = two-phase kernel (a
+ * sweep in passes: the columns' values are first copied, block by block
+ * through shared memory, into a buffer in the order the rows consume them,
+ * then every row sums a contiguous stream in 64-bit fixed point; taken only
+ * when the environment variable CMG_2P=1 is set at cmg_setup, for every
+ * level with a sweep layout).  Staging is chosen at setup where the gathers
+ * it serves are several per staged entry and SM; CMG_STAGE=0 (never) or
+ * CMG_STAGE=1 (every slice level), read by cmg_setup, overrides that rule.
+ * Results do not depend on the kernel beyond rounding; every kernel sums in
+ * a fixed order (or exactly), so repeated solves are bit-identical.
+ * Errors: INVALID_ARG if h is NULL. */
 cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *staged_out);
 
 /* Sweep precision of each level (host int32 array of length >= levels):

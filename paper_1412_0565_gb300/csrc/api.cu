@@ -93,6 +93,8 @@ struct LevelData {
     double g = 0.0;
     bool has_lay = false;   // large level: sweeps read the sweep layout
     SweepLayout lay;
+    bool has_xl = false;    // ... or its two-phase layout (lay then holds only the row order)
+    XLayout xl;
     int fp32 = 0;           // this level's sweeps run in FP32
 };
 
@@ -119,6 +121,7 @@ static void free_level(LevelData &L, cudaStream_t s) {
     dev_free(L.agg, s);
     dev_free(L.tiles, s);
     free_sweep_layout(L.lay, s);
+    free_xlayout(L.xl, s);
     L = LevelData();
 }
 
@@ -224,7 +227,7 @@ cmg_status_t cmg::launch_to_float(long long m, const double *w, float *w32, cuda
 constexpr long long kFp32MinEntries = 1ll << 20;
 
 static PiLevel level_view(const LevelData &L) {
-    PiLevel v;
+    PiLevel v = {};
     v.n = L.n;
     v.nnz = L.nnz;
     v.rp = L.rp;
@@ -237,7 +240,28 @@ static PiLevel level_view(const LevelData &L) {
     v.ntiles = L.ntiles;
     v.sell_nnz = L.sell_nnz;
     v.lay = L.has_lay ? &L.lay : nullptr;
+    v.xl = L.has_xl ? &L.xl : nullptr;
     return v;
+}
+
+// Levels swept through the two-phase layout: only on request (CMG_2P=1,
+// read at setup: every level with a sweep layout).  Measured on the
+// 4.19M-vertex Chung-Lu graph's levels 0-2 it is about twice as slow as the
+// slice kernel (it writes and reads back every gathered value through L2 and
+// restages source blocks each pass), so no level takes it by default.
+static cmg_status_t wants_two_phase(const LevelData &, bool *out, cudaStream_t) {
+    const char *env = getenv("CMG_2P");
+    *out = env && env[0] == '1';
+    return CMG_OK;
+}
+
+// Test knobs of the two-phase layout: CMG_2P_SB (source block vertices),
+// CMG_2P_XCAP (bytes per pass buffer).
+static XParams two_phase_params() {
+    XParams p;
+    if (const char *e = getenv("CMG_2P_SB")) p.sb = atoi(e);
+    if (const char *e = getenv("CMG_2P_XCAP")) p.xcap_bytes = atoll(e);
+    return p;
 }
 
 static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t *row_ptr,
@@ -364,6 +388,25 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
             if (small_level_fits(level_view(L), L.fp32)) continue;
             const int hv[2] = {0, L.n};
             CMG_CUDA(cudaMemcpyAsync(voff1, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
+            bool x2 = false;
+            CMG_TRY(wants_two_phase(L, &x2, s));
+            if (x2) {
+                CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, L.fp32,
+                                           &L.lay, &lay_bytes, s, true));
+                size_t xb = 0;
+                const cmg_status_t st = build_xlayout(L.n, L.nnz, L.rp, L.col, L.w, L.fp32, L.lay.perm, L.lay.inv,
+                                                      two_phase_params(), &L.xl, &xb, s);
+                if (st == CMG_OK) {
+                    L.has_xl = true;
+                    L.has_lay = true;
+                    lay_bytes += xb;
+                    continue;
+                }
+                // beyond the two-phase layout's limits: the slice layout
+                free_xlayout(L.xl, s);
+                free_sweep_layout(L.lay, s);
+                if (st != CMG_ERR_TOO_LARGE) return st;
+            }
             CMG_TRY(build_sweep_layout(1, voff1, std::vector<int>{0, L.n}, L.n, L.rp, L.col, L.w, L.fp32,
                                        &L.lay, &lay_bytes, s));
             L.has_lay = true;
@@ -426,6 +469,7 @@ cmg_status_t cmg::hierarchy_view(cmg_hierarchy_t h, HierarchyView *out) {
         PiLevel v = level_view(L);
         v.w32 = nullptr;
         v.lay = nullptr;
+        v.xl = nullptr;
         out->lv.push_back(v);
     }
     out->device = h->device;
@@ -671,7 +715,8 @@ cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *st
         const LevelData &L = h->lv[j];
         const int staged = L.has_lay ? L.lay.stage_n : 0;
         int kind = 0;
-        if (L.has_lay) kind = staged > 0 ? 2 : 1;
+        if (L.has_xl) kind = 4;
+        else if (L.has_lay) kind = staged > 0 ? 2 : 1;
         else if (!small_level_fits(level_view(L), L.fp32)) kind = 3;
         if (kind_out) kind_out[j] = kind;
         if (staged_out) staged_out[j] = staged;

@@ -92,10 +92,69 @@ constexpr int kHeavyChunk = 2048;
 // Builds the layout of the N rows of a level holding G graphs at union
 // offsets voff (device, G+1; host copy hvoff) from the level's CSR; fp32
 // selects float weights.  Adds its device bytes to *bytes (nullable).
+// perm_only: only the row order (perm, inv), for a level swept through its
+// two-phase layout (no heavy rows, slices or entries).
 cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &hvoff, int N,
                                 const int *rp, const int *col, const double *w, int fp32,
-                                SweepLayout *L, size_t *bytes, cudaStream_t s);
+                                SweepLayout *L, size_t *bytes, cudaStream_t s, bool perm_only = false);
 void free_sweep_layout(SweepLayout &L, cudaStream_t s);
+
+// Two-phase sweep layout of a large single-graph level whose gathers have no
+// locality.  Rows and columns are in the sweep layout's order (perm).  A sweep
+// y = B_g x runs in T passes; pass t owns a contiguous range of rows (about
+// nnz / T entries) and takes two phases:
+//   phase 1: the columns are cut into source blocks of SB vertices; CTA b
+//     copies the source blocks its share of the pass's stream needs into
+//     shared memory and writes x_c of every entry into xbuf, at the entry's
+//     position in list order -- the stream is ordered (source block, dest
+//     block, row, CSR position), so its writes are runs ("cells": one source
+//     block's entries of one dest block) that are contiguous in both orders;
+//   phase 2 (after a grid barrier): the pass's rows are cut into a multiple
+//     of P dest blocks (one or more per CTA); the CTA streams its block's
+//     list -- (row offset, weight, x_c) at consecutive positions -- and adds
+//     each term into a 64-bit fixed-point accumulator of its row in shared
+//     memory (integer adds commute, so every order gives the same sums).
+// Every global access is contiguous; the random accesses are to shared
+// memory only; the sums are exact up to one rounding per term.
+struct XLayout {
+    int P = 0, T = 0, Q = 0, SB = 0, VMAX = 0;
+    long long entries = 0;
+    int ncells = 0;
+    int nblocks = 0;              // dest blocks over all passes
+    size_t smem = 0;              // dynamic shared memory of the sweep kernel
+    long long xcap = 0;           // elements of each of the two xbufs
+    uint16_t *src = nullptr;      // phase-1 stream, pass t from sal[t] on: column - block start
+    uint16_t *dst = nullptr;      // [entries] list order: row - first row of its dest block
+    void *w = nullptr;            // [entries] list order: weights in the sweep precision
+    int *pass_s = nullptr;        // [T + 1] first entry of each pass (both orders)
+    int *sal = nullptr;           // [T + 1] first element of each pass's stream in src (multiples of 8)
+    int *qoff = nullptr;          // [T*(Q+1)] stream offset of each source block within its pass
+    int *ndb = nullptr;           // [T + 1] first dest block of each pass
+    int *dbr = nullptr;           // [nblocks + 1] first row of each dest block
+    int *dbl = nullptr;           // [nblocks + 1] first list entry of each dest block
+    int *cdel = nullptr;          // [ncells] list position - stream position of each cell's entries
+    int *choff = nullptr;         // [T + 1] first chunk of each pass
+    uint2 *chk = nullptr;         // [nchunks] per 32-entry stream chunk: its first entry's cell,
+                                  // and bit l (1..31) set where entry l starts a cell
+    int nchunks = 0;
+    double *pmax = nullptr;       // [2][P] per-CTA max |x| of the sweeps' iterates
+    void *xbuf[2] = {nullptr, nullptr};
+};
+// Knobs of the two-phase layout (0: default).
+struct XParams {
+    int sb = 0;                   // source block vertices
+    long long xcap_bytes = 0;     // bytes of each xbuf (sets the pass count)
+};
+// Builds it from the level's CSR (original ids) and the sweep layout's row
+// order; fp32 selects float weights.  P = the SM count.  Returns
+// CMG_ERR_TOO_LARGE when the level does not fit the layout's limits (the
+// caller then uses the slice layout).  Adds its device bytes to *bytes.
+cmg_status_t build_xlayout(int n, long long nnz, const int *rp, const int *col, const double *w, int fp32,
+                           const uint32_t *perm, const int *inv, const XParams &prm, XLayout *X,
+                           size_t *bytes, cudaStream_t s);
+void free_xlayout(XLayout &X, cudaStream_t s);
+// Dynamic shared memory of the two-phase sweep kernel (FP32 or FP64 sweeps).
+size_t xsweep_smem(int fp32);
 // Adds to *out (zeroed first) the layout entries whose column is below S.
 cmg_status_t layout_count_below(const SweepLayout &L, int S, unsigned long long *out, cudaStream_t s);
 // Iterate entries the staged slice kernel can hold in shared memory (FP32 or
@@ -170,6 +229,8 @@ struct PiLevel {
     // sweep layout (one graph) for the slice kernel, or nullptr; with a layout
     // the level's iterates are stored in the layout's row order
     const SweepLayout *lay;
+    // two-phase layout (same row order as lay), or nullptr
+    const XLayout *xl;
 };
 
 // SELL-32 size of a CSR level (sum over 32-row slices of 32 x longest row);

@@ -183,7 +183,7 @@ __global__ void k_layout_chunk_rows(int h, const int *__restrict__ hchunk, int *
 
 cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &hvoff, int N,
                                 const int *rp, const int *col, const double *w, int fp32,
-                                SweepLayout *L, size_t *bytes, cudaStream_t s) {
+                                SweepLayout *L, size_t *bytes, cudaStream_t s, bool perm_only) {
     int maxn = 0;
     for (int q = 0; q < G; q++) maxn = std::max(maxn, hvoff[q + 1] - hvoff[q]);
     L->col16 = maxn <= 65536 ? 1 : 0;
@@ -216,6 +216,14 @@ cmg_status_t build_sweep_layout(int G, const int *voff, const std::vector<int> &
     CMG_CUDA(cudaMemcpyAsync(L->perm, va, sizeof(uint32_t) * N, cudaMemcpyDeviceToDevice, s));
     k_layout_inv<<<grid_for(N, 256), 256, 0, s>>>(N, L->perm, L->inv);
     CMG_TRY(launch_status());
+    if (perm_only) {
+        L->hheavy.assign(G, 0);
+        L->hecnt.assign(G, 0);
+        L->hmcnt.assign(G, 0);
+        L->entries = 0;
+        if (bytes) *bytes += (size_t)N * 8;
+        return CMG_OK;
+    }
     CMG_TRY(dev_alloc_n(&L->heavy, (size_t)G, s));
     CMG_TRY(dev_alloc_n(&L->eoff, (size_t)G + 1, s));
     CMG_TRY(dev_alloc_n(&L->moff, (size_t)G + 1, s));

@@ -45,8 +45,17 @@ namespace cmg {
 // [sweep][0] loop top, [1] control done, [2] first row warp done, [3] last row warp done
 __device__ long long g_trace[256][8];
 #define TRACE(s, k) do { if ((s) < 256) g_trace[(s)][(k)] = clock64(); } while (0)
+// cycle stamps of the phases of the two-phase kernel's third sweep, per CTA
+// and pass: [b][t][0] pass top, [2] phase 1 done, [3] after the barrier,
+// [5] the last dest block's list summed, [6] its rows completed
+__device__ long long g_x2t[160][32][8];
+#define X2T(s, t, k) do { if ((s) == 2 && (t) < 32 && threadIdx.x == 32 && blockIdx.x < 160) g_x2t[blockIdx.x][(t)][(k)] = clock64(); } while (0)
+extern "C" int cmg_debug_x2_trace(long long *host, int count) {
+    return (int)cudaMemcpyFromSymbol(host, g_x2t, sizeof(long long) * (size_t)count);
+}
 #else
 #define TRACE(s, k) do { } while (0)
+#define X2T(s, t, k) do { } while (0)
 #endif
 
 // Loads of data written by other CTAs of the same launch go through L2.
@@ -115,6 +124,14 @@ struct PiArgs {
     int nchunks;
     int stream_hint;        // the layout is larger than L2: read it evict-first
     int stage_n;            // iterate entries 0..stage_n-1 copied to shared memory per sweep
+    // two-phase kernel: the level's XLayout (see internal.h)
+    int x_T, x_Q, x_SB, x_VMAX;
+    const uint16_t *x_src, *x_dst;
+    const void *x_w;
+    const int *x_ps, *x_sal, *x_qoff, *x_ndb, *x_dbr, *x_dbl, *x_cdel, *x_choff;
+    const uint2 *x_chk;
+    double *x_pmax;
+    void *x_buf[2];
 };
 
 
@@ -842,6 +859,405 @@ __global__ void __launch_bounds__(STAGE ? kStageThreads : kTileThreads, STAGE ? 
     }
 }
 
+// ================================================================== two-phase kernel
+// Sweeps of a level with a two-phase layout (XLayout, internal.h): one
+// 1024-thread CTA per SM (grid = the layout's P), warp 0 the control warp,
+// warps 1..31 the row warps.  Per pass: phase 1 (source blocks staged in
+// shared memory, xbuf written in list order), a grid barrier, phase 2 (the
+// CTA's dest blocks: terms added into 64-bit fixed-point row accumulators in
+// shared memory, then the rows completed).  The two xbufs alternate between
+// passes, so phase 1 of pass t+1 follows phase 2 of pass t without a
+// barrier: the buffer it overwrites was last read in pass t-1, which every
+// CTA finished before the barrier of pass t.
+//
+// Fixed point: a sweep's terms are w x_c (FP64 form) or w (x_r - x_c) (FP32
+// form), so every partial sum of a row is at most g max|x| in magnitude (g
+// is twice the largest weighted degree).  With sc = 61 - e, g max|x| < 2^e,
+// the terms scaled by 2^sc and rounded to integers sum in int64 without
+// overflow; integer addition is associative, so the sum does not depend on
+// the order of the shared-memory atomics.  max|x| of the sweep's iterate is
+// the exact maximum of the previous sweep's per-CTA maxima.
+constexpr int kXRows = kStageThreads / 32 - 1;   // row warps
+
+// round(v 2^sc) for a double, by integer arithmetic (round half away from
+// zero; values below 2^-sc / 2 and subnormals give 0): the FP64 pipe is
+// left to the product that forms v
+__device__ __forceinline__ long long fix64(double v, int sc) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int ef = (int)((b >> 52) & 0x7ffu);
+    if (ef == 0) return 0;
+    const long long mant = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);
+    const int sh = ef - 1075 + sc;   // v 2^sc = mant 2^sh; sh <= 8 by the choice of sc
+    long long r;
+    if (sh >= 0) r = mant << min(sh, 10);
+    else if (sh > -64) r = (mant + (1ll << (-sh - 1))) >> (-sh);
+    else r = 0;
+    return (b >> 63) ? -r : r;
+}
+
+__device__ __forceinline__ long long fix_term(float v, int sc, float scf) { return __float2ll_rn(v * scf); }
+__device__ __forceinline__ long long fix_term(double v, int sc, float) { return fix64(v, sc); }
+
+__device__ __forceinline__ int fix_scale(double g, double xmax) {
+    if (!(xmax > 0.0)) return 0;
+    int ex;
+    frexp(g * xmax, &ex);   // g xmax < 2^ex
+    return max(-120, min(120, 61 - ex));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStageThreads, 1) k_power_2p(PiArgs a, GridSync *gs) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sm = reinterpret_cast<T *>(smem_raw);
+    __shared__ Part s_pw[kStageThreads / 32];
+    __shared__ double s_mx[kStageThreads / 32];
+    __shared__ Slot s_slot[2];
+    __shared__ int s_sc;
+    __shared__ Ctl s_ctl;   // the control warp's state (kept out of every thread's registers)
+    const int n = a.n;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int rt = tid - 32, nrt = (int)blockDim.x - 32, rw = warp - 1;   // row threads and warps
+    T *const ring0 = (T *)a.buf[0], *const ring1 = (T *)a.buf[1], *const ring2 = (T *)a.buf[2];
+    const bool fp64 = sizeof(T) == 8;
+    const T g = (T)a.g;
+    const float inv_gf = 1.0f / (float)a.g;
+    const int P = (int)gridDim.x, b = (int)blockIdx.x;
+    const int r0 = (int)((long long)n * b / P), r1 = (int)((long long)n * (b + 1) / P);
+    const T *__restrict__ XW = reinterpret_cast<const T *>(a.x_w);
+    auto cta_max = [&](double v, double *dst) {   // max over the CTA into *dst (thread 0 writes)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) s_mx[warp] = v;
+        __syncthreads();
+        if (warp == 0) {
+            double u = lane < (int)(blockDim.x >> 5) ? s_mx[lane] : 0.0;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+            if (lane == 0) *dst = u;
+        }
+    };
+    auto grid_max = [&](const double *src) {      // warp 0: max of the P per-CTA values
+        double u = 0.0;
+        for (int k = lane; k < P; k += 32) u = fmax(u, __ldcg(src + k));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) u = fmax(u, __shfl_xor_sync(0xffffffffu, u, o));
+        return u;
+    };
+
+    // ---------------------------------------------------------- start phase
+    {
+        const void *cb = nullptr;
+        double cmu = 0.0, cinv = 0.0;
+        if (a.start == 1) {
+            cb = a.cbuf[a.cres->buf];
+            cmu = a.cres->mu;
+            cinv = a.cres->inv_s;
+        }
+        Part acc = part_zero();
+        double mx = 0.0;
+        for (int p = r0 + tid; p < r1; p += blockDim.x) {
+            const int old = a.perm[p];
+            const T xt = (T)start_value(a, old, cb, cmu, cinv);
+            ring0[p] = xt;
+            mx = fmax(mx, fabs((double)xt));
+            if (fp64) {
+                double d = 0.0;
+                for (int e = __ldg(a.rp + old), e1 = __ldg(a.rp + old + 1); e < e1; e++) d += __ldg(a.w + e);
+                a.gd[p] = a.g - d;
+            }
+            const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
+            acc.A = ff_add(acc.A, v);
+            acc.B = ff_add(acc.B, ff_mul(v, v));
+        }
+        Part p = warp_sum_part(acc);
+        if (lane == 0) s_pw[warp] = p;
+        cta_max(mx, a.x_pmax + b);   // its __syncthreads also publishes s_pw
+        if (warp == 0) {
+            Part q = (lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + (size_t)blockIdx.x * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+    }
+    if (!grid_sync(gs)) return;
+    if (warp == 0) {
+        Ctl c;
+        Part q = part_zero();
+        for (int k = lane; k < P; k += 32) {
+            const ff *src = a.partials + (size_t)k * 3;
+            Part t;
+            t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+            t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+            t.C = ff_zero();
+            q = part_add(q, t);
+        }
+        q = warp_sum_part(q);
+        const double xmax = grid_max(a.x_pmax);
+        const double mu0 = to_d(q.A) / (double)n;
+        double ss0 = to_d(q.B) - (double)n * mu0 * mu0;
+        if (ss0 < 0.0) ss0 = 0.0;
+        const int e0 = start_exponent(ss0);
+        ctl_init(c, a, mu0, ss0, e0);
+        if (lane == 0) {
+            s_ctl = c;
+            s_slot[1] = slot_make(ff_from_double(mu0), e0, a.g, fp64);
+            s_slot[0] = slot_make(ff_zero(), 0, a.g, fp64);
+            s_sc = fix_scale(a.g, xmax);
+        }
+    }
+    __syncthreads();
+
+    const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
+    int s = 0;
+    int exit_kind = no_sweeps ? 2 : 0;
+    while (!no_sweeps) {
+        const Slot sl = s_slot[(s + 1) & 1];
+        if (sl.stop) {
+            exit_kind = 1;
+            break;
+        }
+        if ((a.mode == 1 && s >= a.k_fixed) || (a.mode == 0 && s >= a.max_sweeps)) {
+            exit_kind = 2;
+            break;
+        }
+        const T *x = pick3<T *>(ring0, ring1, ring2, s % 3);
+        T *y = pick3<T *>(ring0, ring1, ring2, (s + 1) % 3);
+        if (warp == 0 && s >= 1) {
+            // decisions of sweep s-1 and the fixed-point scale of sweep s,
+            // overlapped with phase 1 of pass 0 (published by its barrier)
+            Part q = part_zero();
+            const ff *base = a.partials + (size_t)(s & 1) * P * 3;
+            for (int k = lane; k < P; k += 32) {
+                const ff *src = base + (size_t)k * 3;
+                Part t;
+                t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                q = part_add(q, t);
+            }
+            q = warp_sum_part(q);
+            Slot nx;
+            Ctl c = s_ctl;
+            ctrl_step(a, s, q, c, &nx, false, fp64);
+            const double xmax = grid_max(a.x_pmax + (size_t)(s & 1) * P);
+            __syncwarp();
+            if (lane == 0) {
+                s_ctl = c;
+                s_slot[s & 1] = nx;
+                s_sc = fix_scale(a.g, xmax);
+            }
+        }
+        const T m = fp64 ? (T)sl.m_d : (T)sl.m.hi;
+        const T sig = fp64 ? (T)sl.sig_d : (T)scale2f(inv_gf, sl.e);
+        const T gm = fp64 ? (T)sl.gm_d : g * m;
+        Acc<T> acc;
+        acc.reset();
+        T ymax = (T)0;
+        auto finish = [&](int i, T xi, T ac) {
+            T yv;
+            if (fp64) yv = (T)((fma(a.gd[i], (double)xi, (double)ac) - (double)gm) * (double)sig);
+            else yv = (g * (xi - m) - ac) * sig;
+            y[i] = yv;
+            acc.add(yv, xi);
+            ymax = max(ymax, abs(yv));
+        };
+        for (int t = 0; t < a.x_T; t++) {
+            // xbuf holds pass t's list positions from ps0 & ~7 on, so that 8
+            // list entries at a multiple of 8 sit at a multiple of 8 there
+            T *const xb = reinterpret_cast<T *>(a.x_buf[t & 1]);
+            const int ps0 = __ldg(a.x_ps + t), xsh = ps0 & 7, xb0 = ps0 - xsh;
+            X2T(s, t, 0);
+            if (warp > 0) {
+                // ------------------------------------------------ phase 1
+                // this CTA's share of the pass's stream, source block by
+                // source block; entry j goes to its list position, found
+                // from its 32-entry chunk's cell and cell-start bits
+                const long long Et = (long long)__ldg(a.x_ps + t + 1) - ps0;
+                int e = (int)(Et * b / P);
+                const int e1 = (int)(Et * (b + 1) / P);
+                const int *qo = a.x_qoff + (size_t)t * (a.x_Q + 1);
+                const uint2 *chk = a.x_chk + __ldg(a.x_choff + t);
+                const uint16_t *srcp = a.x_src + __ldg(a.x_sal + t);
+                int lo = 0, hi = a.x_Q - 1;   // last block q with qo[q] <= e
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (__ldg(qo + mid) <= e) lo = mid;
+                    else hi = mid - 1;
+                }
+                for (int q = lo; e < e1; q++) {
+                    const int qe = min(e1, __ldg(qo + q + 1));
+                    if (qe > e) {
+                        const int base = q * a.x_SB, cnt = min(a.x_SB, n - base);
+                        const T *xs = x + base;
+                        // 16-byte asynchronous copies (L2 only: x was written
+                        // by other CTAs before the last barrier), then the tail
+                        const int nv16 = ((reinterpret_cast<uintptr_t>(xs) & 15) == 0) ? (int)((cnt * sizeof(T)) / 16) : 0;
+                        for (int k = rt; k < nv16; k += nrt) {
+                            const unsigned dsm = (unsigned)__cvta_generic_to_shared(reinterpret_cast<char *>(sm) + 16 * (size_t)k);
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dsm),
+                                         "l"(reinterpret_cast<const char *>(xs) + 16 * (size_t)k)
+                                         : "memory");
+                        }
+                        asm volatile("cp.async.wait_all;" ::: "memory");
+                        for (int k = nv16 * (int)(16 / sizeof(T)) + rt; k < cnt; k += nrt) sm[k] = __ldcg(xs + k);
+                        bar_rows(nrt);
+                        // 8 consecutive stream entries per row thread (one
+                        // vector load of their source offsets); an entry's
+                        // cell comes from its 32-entry chunk's bits
+                        for (int gi = (e >> 3) + rt; 8 * gi < qe; gi += nrt) {
+                            const int j0 = 8 * gi;
+                            const uint4 sv = __ldcs(reinterpret_cast<const uint4 *>(srcp + j0));
+                            const uint2 ci = __ldg(chk + (j0 >> 5));
+                            const unsigned sw[4] = {sv.x, sv.y, sv.z, sv.w};
+                            int lastc = -1, dl = 0;
+#pragma unroll
+                            for (int u = 0; u < 8; u++) {
+                                const int j = j0 + u;
+                                if (j < e || j >= qe) continue;
+                                const int cell = (int)ci.x + __popc(ci.y & ((2u << (j & 31)) - 1u));
+                                if (cell != lastc) {
+                                    dl = __ldg(a.x_cdel + cell);
+                                    lastc = cell;
+                                }
+                                xb[j + xsh + dl] = sm[(sw[u >> 1] >> (16 * (u & 1))) & 0xffffu];
+                            }
+                        }
+                        bar_rows(nrt);
+                    }
+                    e = qe;
+                }
+            }
+            X2T(s, t, 2);
+            if (!grid_sync(gs)) return;
+            X2T(s, t, 3);
+            if (warp > 0) {
+                // ------------------------------------------------ phase 2
+                const int sc = s_sc;
+                const float scf = ldexpf(1.0f, sc);
+                long long *const accs = reinterpret_cast<long long *>(smem_raw);
+                T *const xv = reinterpret_cast<T *>(accs + a.x_VMAX);
+                const int g0 = __ldg(a.x_ndb + t), g1 = __ldg(a.x_ndb + t + 1);
+                for (int gb = g0 + b; gb < g1; gb += P) {
+                    const int R0 = __ldg(a.x_dbr + gb), R1 = __ldg(a.x_dbr + gb + 1);
+                    const int L0 = __ldg(a.x_dbl + gb), L1 = __ldg(a.x_dbl + gb + 1);
+                    for (int p = R0 + rt; p < R1; p += nrt) {
+                        xv[p - R0] = __ldcg(x + p);
+                        accs[p - R0] = 0;
+                    }
+                    bar_rows(nrt);
+                    // 8 consecutive list entries per lane (vector loads from
+                    // a multiple of 8); a run of one row's entries is summed
+                    // in a register and added to its accumulator once
+                    for (int pb = (L0 & ~7) + 256 * rw; pb < L1; pb += 256 * kXRows) {
+                        const int base = pb + 8 * lane;
+                        if (base + 8 <= L0 || base >= L1) continue;
+                        const uint4 dv = __ldcs(reinterpret_cast<const uint4 *>(a.x_dst + base));
+                        const unsigned dw[4] = {dv.x, dv.y, dv.z, dv.w};
+                        T wv[8], xvv[8];
+                        if (fp64) {
+#pragma unroll
+                            for (int h = 0; h < 4; h++) {
+                                const double2 w2 = __ldcs(reinterpret_cast<const double2 *>(XW + base) + h);
+                                const double2 x2 = __ldcg(reinterpret_cast<const double2 *>(xb + (base - xb0)) + h);
+                                wv[2 * h] = (T)w2.x;
+                                wv[2 * h + 1] = (T)w2.y;
+                                xvv[2 * h] = (T)x2.x;
+                                xvv[2 * h + 1] = (T)x2.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 2; h++) {
+                                const float4 w4 = __ldcs(reinterpret_cast<const float4 *>(XW + base) + h);
+                                const float4 x4 = __ldcg(reinterpret_cast<const float4 *>(xb + (base - xb0)) + h);
+                                wv[4 * h] = (T)w4.x;
+                                wv[4 * h + 1] = (T)w4.y;
+                                wv[4 * h + 2] = (T)w4.z;
+                                wv[4 * h + 3] = (T)w4.w;
+                                xvv[4 * h] = (T)x4.x;
+                                xvv[4 * h + 1] = (T)x4.y;
+                                xvv[4 * h + 2] = (T)x4.z;
+                                xvv[4 * h + 3] = (T)x4.w;
+                            }
+                        }
+                        int rd = -1;
+                        long long ra = 0;
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const int pos = base + k;
+                            if (pos < L0 || pos >= L1) continue;
+                            const int d = (int)((dw[k >> 1] >> (16 * (k & 1))) & 0xffffu);
+                            const T v = fp64 ? wv[k] * xvv[k] : wv[k] * (xv[d] - xvv[k]);
+                            const long long iv = fix_term(v, sc, scf);
+                            if (d != rd) {
+                                if (rd >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(accs + rd), (unsigned long long)ra);
+                                rd = d;
+                                ra = iv;
+                            } else {
+                                ra += iv;
+                            }
+                        }
+                        if (rd >= 0) atomicAdd(reinterpret_cast<unsigned long long *>(accs + rd), (unsigned long long)ra);
+                    }
+                    bar_rows(nrt);
+                    X2T(s, t, 5);
+                    for (int p = R0 + rt; p < R1; p += nrt) {
+                        T ac;
+                        if (fp64) ac = (T)((double)accs[p - R0] * ldexp(1.0, -sc));
+                        else ac = (T)(__ll2float_rn(accs[p - R0]) * ldexpf(1.0f, -sc));
+                        finish(p, xv[p - R0], ac);
+                    }
+                    bar_rows(nrt);
+                }
+                X2T(s, t, 6);
+            }
+        }
+        if (warp > 0) {
+            Part p = warp_sum_part(acc.get());
+            if (lane == 0) s_pw[warp] = p;
+        }
+        cta_max((double)ymax, a.x_pmax + (size_t)((s + 1) & 1) * P + b);   // its __syncthreads publishes s_pw
+        if (warp == 0) {
+            Part q = (lane >= 1 && lane < (int)(blockDim.x >> 5)) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
+            if (lane == 0) {
+                ff *dst = a.partials + ((size_t)((s + 1) & 1) * P + blockIdx.x) * 3;
+                dst[0] = q.A;
+                dst[1] = q.B;
+                dst[2] = q.C;
+            }
+        }
+        if (!grid_sync(gs)) return;
+        s++;
+    }
+    // ---------------------------------------------------------- result
+    if (warp == 0) {
+        Ctl c = s_ctl;
+        if (exit_kind == 2 && !no_sweeps) {
+            Part q = part_zero();
+            const ff *base = a.partials + (size_t)(s & 1) * P * 3;
+            for (int k = lane; k < P; k += 32) {
+                const ff *src = base + (size_t)k * 3;
+                Part t;
+                t.A = ff_make(LDX(&src[0].hi), LDX(&src[0].lo));
+                t.B = ff_make(LDX(&src[1].hi), LDX(&src[1].lo));
+                t.C = ff_make(LDX(&src[2].hi), LDX(&src[2].lo));
+                q = part_add(q, t);
+            }
+            q = warp_sum_part(q);
+            ctrl_step(a, s, q, c, nullptr, true, fp64);
+        }
+        if (blockIdx.x == 0 && lane == 0) {
+            const int rs = c.res_sweep;
+            const int rb = c.zero ? (rs - 1) % 3 : rs % 3;
+            write_result(a, c, rb, (rs + 2) % 3);
+        }
+    }
+}
+
 // ================================================================== small kernel
 // Shared memory: ring[3][n] T, gd[n] (FP64 form), w[E] T, rp[n+1] int,
 // col[E] int, slice offsets[n/32 + 2] int.  E = nnz (CSR) or the SELL-32
@@ -1230,6 +1646,19 @@ static size_t small_bytes(const PiLevel &lv, int G, int fp32) {
     return small_smem_bytes<double>(lv.n, e) + 8 + 48 * (size_t)small_threads(lv.n, G);
 }
 
+size_t xsweep_smem(int fp32) {
+    DeviceInfo d;
+    if (device_info(&d) != CMG_OK) return 0;
+    cudaFuncAttributes fa;
+    const void *k = fp32 ? (const void *)k_power_2p<float> : (const void *)k_power_2p<double>;
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return 0;
+    const long long room = (long long)d.max_smem_optin - (long long)fa.sharedSizeBytes - 256;
+    // 192 KB: a 48K-vertex FP32 (24K FP64) source block, 24K (12K) vrows
+    const long long want = 192ll << 10;
+    if (room < (64ll << 10)) return 0;
+    return (size_t)(std::min(room, want) & ~255ll);
+}
+
 int stage_capacity(int fp32) {
     DeviceInfo d;
     if (device_info(&d) != CMG_OK) return 0;
@@ -1332,6 +1761,44 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
         return coop_launch(kern, 1, small_threads(lv.n, G), smem, s, args, gs);
     }
     if (!run.fp32 && !run.gd) return CMG_ERR_INVALID_ARG;
+    if (lv.xl && lv.lay) {
+        // two-phase kernel: one 1024-thread CTA per SM, the layout's P CTAs
+        const XLayout &X = *lv.xl;
+        a.perm = reinterpret_cast<const int *>(lv.lay->perm);
+        a.x_T = X.T;
+        a.x_Q = X.Q;
+        a.x_SB = X.SB;
+        a.x_VMAX = X.VMAX;
+        a.x_src = X.src;
+        a.x_dst = X.dst;
+        a.x_w = X.w;
+        a.x_ps = X.pass_s;
+        a.x_sal = X.sal;
+        a.x_qoff = X.qoff;
+        a.x_ndb = X.ndb;
+        a.x_dbr = X.dbr;
+        a.x_dbl = X.dbl;
+        a.x_cdel = X.cdel;
+        a.x_choff = X.choff;
+        a.x_chk = X.chk;
+        a.x_pmax = X.pmax;
+        a.x_buf[0] = X.xbuf[0];
+        a.x_buf[1] = X.xbuf[1];
+        const void *kern = run.fp32 ? (const void *)k_power_2p<float> : (const void *)k_power_2p<double>;
+        CMG_TRY(allow_max_dynamic_smem(kern));
+        int maxb = 0;
+        CMG_TRY(coop_max_blocks(kern, kStageThreads, X.smem, &maxb));
+        if (maxb < X.P) return CMG_ERR_TOO_LARGE;
+        double *partials;
+        if (ws) {
+            if (2 * X.P * 3 > ws->partials_cap) return CMG_ERR_TOO_LARGE;
+            partials = ws->partials;
+        } else {
+            CMG_TRY(scr.get(&partials, (size_t)2 * X.P * 3));
+        }
+        a.partials = reinterpret_cast<ff *>(partials);
+        return coop_launch(kern, X.P, kStageThreads, X.smem, s, args, gs);
+    }
     if (lv.lay) {
         // slice kernel over the level's sweep layout (one graph)
         const SweepLayout &L = *lv.lay;
