@@ -678,7 +678,7 @@ def oracle_checks(args, c2_graph, r64, r32, batch, chung_lu, stream):
     return out
 
 
-KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled", 4: "two-phase"}
+KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled", 4: "two-phase", 5: "cluster"}
 
 TABLE4 = os.path.join(ROOT, "tests", "golden", "table4_gcmg.txt")
 
@@ -1038,7 +1038,7 @@ def run_chung_lu(args, stream, flush):
     return out
 
 
-KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled", 4: "two-phase"}
+KERNEL_KIND = {0: "smem", 1: "slice", 2: "slice+staged", 3: "tiled", 4: "two-phase", 5: "cluster"}
 
 
 def run_serving(args):

@@ -237,7 +237,11 @@ cmg_status_t cmg_hierarchy_info(cmg_hierarchy_t h, int32_t *levels, int64_t *n_p
  * through shared memory, into a buffer in the order the rows consume them,
  * then every row sums a contiguous stream in 64-bit fixed point; taken only
  * when the environment variable CMG_2P=1 is set at cmg_setup, for every
- * level with a sweep layout).  Staging is chosen at setup where the gathers
+ * level with a sweep layout), 5 = cluster kernel (FP64 sweeps of a level of
+ * 512 to a few thousand rows spread over one thread-block cluster of 2 to 8
+ * CTAs: every CTA holds the iterate, computes its share of the rows and
+ * stores them into the others' shared memory; chosen at setup unless
+ * CMG_CLUSTER=0).  Staging is chosen at setup where the gathers
  * it serves are several per staged entry and SM; CMG_STAGE=0 (never) or
  * CMG_STAGE=1 (every slice level), read by cmg_setup, overrides that rule.
  * Results do not depend on the kernel beyond rounding; every kernel sums in

@@ -327,7 +327,7 @@ class Hierarchy:
     def level_kernels(self):
         """Per level: (kind, staged) -- kind 0 shared-memory kernel, 1 slice
         kernel, 2 slice kernel with `staged` iterate entries staged in shared
-        memory, 3 row-tile kernel, 4 two-phase kernel."""
+        memory, 3 row-tile kernel, 4 two-phase kernel, 5 cluster kernel."""
         L = self.levels
         kind = np.zeros(L, dtype=np.int32)
         staged = np.zeros(L, dtype=np.int32)

@@ -95,6 +95,8 @@ struct LevelData {
     SweepLayout lay;
     bool has_xl = false;    // ... or its two-phase layout (lay then holds only the row order)
     XLayout xl;
+    int cl_ctas = 0, cl_threads = 0, cl_emax = 0;   // FP64 sweeps in one cluster (cluster_plan)
+    size_t cl_smem = 0;
     int fp32 = 0;           // this level's sweeps run in FP32
 };
 
@@ -241,6 +243,10 @@ static PiLevel level_view(const LevelData &L) {
     v.sell_nnz = L.sell_nnz;
     v.lay = L.has_lay ? &L.lay : nullptr;
     v.xl = L.has_xl ? &L.xl : nullptr;
+    v.cl_ctas = L.cl_ctas;
+    v.cl_threads = L.cl_threads;
+    v.cl_emax = L.cl_emax;
+    v.cl_smem = L.cl_smem;
     return v;
 }
 
@@ -374,7 +380,24 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         CMG_TRY(dev_alloc_n(&L.w32, (size_t)std::max<long long>(L.nnz, 1), s));
         CMG_TRY(launch_to_float(L.nnz, L.w, L.w32, s));
     }
-    // ---- sweep layouts for the levels the shared-memory kernel cannot hold
+    // ---- FP64 levels of 512 to a few thousand rows: sweeps in one thread-
+    // block cluster (every CTA holds the iterate; rows split over the SMs)
+    if (!getenv("CMG_CLUSTER") || getenv("CMG_CLUSTER")[0] != '0') {
+        std::vector<int> rph;
+        for (auto &L : h->lv) {
+            if (L.fp32 || L.n < 512 || L.n > 65536) continue;
+            rph.resize((size_t)L.n + 1);
+            CMG_CUDA(cudaMemcpyAsync(rph.data(), L.rp, sizeof(int) * ((size_t)L.n + 1), cudaMemcpyDeviceToHost, s));
+            CMG_CUDA(cudaStreamSynchronize(s));
+            PiLevel v = level_view(L);
+            cluster_plan(&v, rph.data());
+            L.cl_ctas = v.cl_ctas;
+            L.cl_threads = v.cl_threads;
+            L.cl_emax = v.cl_emax;
+            L.cl_smem = v.cl_smem;
+        }
+    }
+    // ---- sweep layouts for the levels the shared-memory kernels cannot hold
     size_t lay_bytes = 0;
     std::vector<int> stage_try(nlev, 0);
     std::vector<unsigned long long> below(nlev, 0);
@@ -385,7 +408,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         CMG_TRY(scr.get(&below_dev, (size_t)nlev));
         for (int k = 0; k < nlev; k++) {
             LevelData &L = h->lv[k];
-            if (small_level_fits(level_view(L), L.fp32)) continue;
+            if (L.cl_ctas > 0 || small_level_fits(level_view(L), L.fp32)) continue;
             const int hv[2] = {0, L.n};
             CMG_CUDA(cudaMemcpyAsync(voff1, hv, sizeof(hv), cudaMemcpyHostToDevice, s));
             bool x2 = false;
@@ -470,6 +493,7 @@ cmg_status_t cmg::hierarchy_view(cmg_hierarchy_t h, HierarchyView *out) {
         v.w32 = nullptr;
         v.lay = nullptr;
         v.xl = nullptr;
+        v.cl_ctas = 0;
         out->lv.push_back(v);
     }
     out->device = h->device;
@@ -715,7 +739,8 @@ cmg_status_t cmg_level_kernels(cmg_hierarchy_t h, int32_t *kind_out, int32_t *st
         const LevelData &L = h->lv[j];
         const int staged = L.has_lay ? L.lay.stage_n : 0;
         int kind = 0;
-        if (L.has_xl) kind = 4;
+        if (L.cl_ctas > 0) kind = 5;
+        else if (L.has_xl) kind = 4;
         else if (L.has_lay) kind = staged > 0 ? 2 : 1;
         else if (!small_level_fits(level_view(L), L.fp32)) kind = 3;
         if (kind_out) kind_out[j] = kind;

@@ -231,7 +231,19 @@ struct PiLevel {
     const SweepLayout *lay;
     // two-phase layout (same row order as lay), or nullptr
     const XLayout *xl;
+    // FP64 sweeps in one thread-block cluster (cluster_plan): CTAs (0: not
+    // planned), threads per CTA, dynamic shared memory per CTA, and the
+    // largest SELL-32 entry count a CTA holds
+    int cl_ctas, cl_threads, cl_emax;
+    size_t cl_smem;
 };
+
+// Plans a level's FP64 sweeps in one thread-block cluster of 2..8 CTAs,
+// each holding the whole iterate ring and the SELL-32 slices of its share
+// of the rows, from the level's row pointers (host copy, n + 1).  Leaves
+// lv->cl_ctas at 0 when the level is outside the plan's range or no cluster
+// of that size can be resident.
+void cluster_plan(PiLevel *lv, const int *rp_host);
 
 // SELL-32 size of a CSR level (sum over 32-row slices of 32 x longest row);
 // dev_counter: one device unsigned long long of scratch.  Synchronises s.

@@ -132,6 +132,7 @@ struct PiArgs {
     const uint2 *x_chk;
     double *x_pmax;
     void *x_buf[2];
+    int cl_emax;            // cluster kernel: SELL-32 entries each CTA holds (at most)
 };
 
 
@@ -1541,6 +1542,341 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     }
 }
 
+// ================================================================== cluster kernel
+// FP64 sweeps of a level spread over one thread-block cluster of C CTAs
+// (2..8, one per SM).  Every CTA holds the whole iterate ring (3 n doubles)
+// and g - d_i of every row, and the SELL-32 slices of its share of the rows
+// (slices split into C ranges of about equal SELL size).  A sweep: the row
+// warps compute their rows from the local iterate and store each y_i into
+// every CTA's ring (distributed shared memory); the control warp sums the
+// CTA's stop sums (fixed order) and stores the three totals into every CTA's
+// slot [sweep parity][rank]; then the cluster meets at its barrier.  Every
+// CTA's control warp sums the C slots in rank order and takes the same
+// decisions, so all CTAs run the same sweeps and reach the same barriers.
+// A CTA is at most one sweep ahead of another (one barrier per sweep), so
+// two slot parities and the ring of three keep stores and reads apart.
+constexpr int kClusterMax = 8;
+// Below this many rows one CTA's sweep (the one-CTA kernel) is faster: the
+// cluster's per-sweep barrier and exchange cost more than the FP64 work it
+// spreads (measured: 245 rows, 3.5 against 2.7 us per sweep).
+constexpr int kClusterMinRows = 512;
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_ctas() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+// every thread of every CTA of the cluster; orders the distributed
+// shared-memory stores before it with the reads after it
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void st_cluster_f64(double *local, unsigned cta, double v) {
+    const unsigned la = (unsigned)__cvta_generic_to_shared(local);
+    unsigned ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(cta));
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+}
+
+// First slice of each of C ranges of about equal SELL-32 size, from the
+// prefix sums pre[0..nsl] of the slices' sizes (the host plans with the same
+// arithmetic).
+__host__ __device__ __forceinline__ int cluster_split(const int *pre, int nsl, int C, int r) {
+    if (r <= 0) return 0;
+    if (r >= C) return nsl;
+    const long long target = (long long)pre[nsl] * r / C;
+    int lo = 0, hi = nsl;   // first q with pre[q] >= target
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if ((long long)pre[mid] < target) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, GridSync *) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n = a.n, nsl = (n + 31) / 32;
+    const int C = (int)cluster_ctas();
+    const unsigned rank = cluster_rank();
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nw = blockDim.x >> 5, nrw = nw - 1, rw = warp - 1;
+    double *ring0 = reinterpret_cast<double *>(smem_raw);
+    double *s_gd = ring0 + 3 * (size_t)n;
+    double *s_part = s_gd + n;                            // [2][kClusterMax][3]
+    double *s_dacc = s_part + 2 * kClusterMax * 3;        // [2][blockDim][3]
+    double *s_w = s_dacc + 2 * (size_t)blockDim.x * 3;    // [emax]
+    int *s_col = reinterpret_cast<int *>(s_w + a.cl_emax);
+    int *s_pre = s_col + a.cl_emax;                       // [nsl + 1]
+    __shared__ Part s_pw[32];
+    __shared__ Slot s_slot[2];
+    __shared__ int s_q[2];
+    const double g = a.g;
+
+    // ---- the slices' SELL-32 sizes, this CTA's range and its entries
+    for (int q = tid; q < nsl; q += blockDim.x) {
+        int L = 0;
+        for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, a.rp[r + 1] - a.rp[r]);
+        s_pre[q + 1] = 32 * L;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        s_pre[0] = 0;
+        for (int q = 0; q < nsl; q++) s_pre[q + 1] += s_pre[q];
+        s_q[0] = cluster_split(s_pre, nsl, C, (int)rank);
+        s_q[1] = cluster_split(s_pre, nsl, C, (int)rank + 1);
+    }
+    __syncthreads();
+    const int q0 = s_q[0], q1 = s_q[1], e_base = s_pre[q0];
+    for (int i = 32 * q0 + tid; i < 32 * q1; i += blockDim.x) {
+        const int q = i >> 5, l = i & 31;
+        const int L = (s_pre[q + 1] - s_pre[q]) >> 5;
+        const int e0 = (i < n) ? a.rp[i] : 0;
+        const int len = (i < n) ? a.rp[i + 1] - e0 : 0;
+        for (int k = 0; k < L; k++) {
+            const int idx = s_pre[q] - e_base + 32 * k + l;
+            if (k < len) {
+                s_col[idx] = a.col[e0 + k];
+                s_w[idx] = a.w[e0 + k];
+            } else {
+                s_col[idx] = (i < n) ? i : 0;   // zero weight: no contribution
+                s_w[idx] = 0.0;
+            }
+        }
+    }
+    for (int k = tid; k < 2 * kClusterMax * 3; k += blockDim.x) s_part[k] = 0.0;
+    // ---- start vector and g - d_i of every row (the same in every CTA)
+    {
+        const void *cb = nullptr;
+        double cmu = 0.0, cinv = 0.0;
+        if (a.start == 1) {
+            cb = a.cbuf[a.cres->buf];
+            cmu = a.cres->mu;
+            cinv = a.cres->inv_s;
+        }
+        Part acc = part_zero();
+        for (int i = tid; i < n; i += blockDim.x) {
+            const double xt = start_value(a, i, cb, cmu, cinv);
+            ring0[i] = xt;
+            double d = 0.0;
+            for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
+            s_gd[i] = g - d;
+            const ff v = ff_from_double(xt);
+            acc.A = ff_add(acc.A, v);
+            acc.B = ff_add(acc.B, ff_mul(v, v));
+        }
+        Part p = warp_sum_part(acc);
+        if (lane == 0) s_pw[warp] = p;
+    }
+    __syncthreads();
+    Ctl c;
+    if (warp == 0) {
+        Part q = (lane < nw) ? s_pw[lane] : part_zero();
+        q = warp_sum_part(q);
+        const double mu0 = to_d(q.A) / (double)n;
+        double ss0 = to_d(q.B) - (double)n * mu0 * mu0;
+        if (ss0 < 0.0) ss0 = 0.0;
+        const int e0 = start_exponent(ss0);
+        ctl_init(c, a, mu0, ss0, e0);
+        if (lane == 0) {
+            s_slot[1] = slot_make(ff_from_double(mu0), e0, a.g, true);
+            s_slot[0] = slot_make(ff_zero(), 0, a.g, true);
+        }
+    }
+    __syncthreads();
+    // every CTA's shared memory is set up before any CTA stores into it
+    cluster_barrier();
+
+    // the C CTAs' totals of parity par, summed in rank order (lane 0), then
+    // given to every lane of the control warp
+    auto cluster_part = [&](int par) -> Part {
+        double A = 0.0, B = 0.0, Cc = 0.0;
+        if (lane == 0)
+            for (int r = 0; r < C; r++) {
+                const double *src = s_part + ((size_t)par * kClusterMax + r) * 3;
+                A += src[0];
+                B += src[1];
+                Cc += src[2];
+            }
+        Part p;
+        p.A = ff_from_double(__shfl_sync(0xffffffffu, A, 0));
+        p.B = ff_from_double(__shfl_sync(0xffffffffu, B, 0));
+        p.C = ff_from_double(__shfl_sync(0xffffffffu, Cc, 0));
+        return p;
+    };
+
+    const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
+    int s = 0;
+    int exit_kind = no_sweeps ? 2 : 0;
+    while (!no_sweeps) {
+        const Slot sl = s_slot[(s + 1) & 1];
+        if (sl.stop) {
+            exit_kind = 1;
+            break;
+        }
+        if ((a.mode == 1 && s >= a.k_fixed) || (a.mode == 0 && s >= a.max_sweeps)) {
+            exit_kind = 2;
+            break;
+        }
+        const double *x = ring0 + (size_t)(s % 3) * n;
+        double *y = ring0 + (size_t)((s + 1) % 3) * n;
+        if (warp == 0) {
+            if (s >= 1) {
+                const Part q = cluster_part((s - 1) & 1);
+                Slot nx;
+                ctrl_step(a, s, q, c, &nx, false, true);
+                if (lane == 0) s_slot[s & 1] = nx;
+            }
+        } else {
+            const double mT = sl.m_d, sig = sl.sig_d, gm = sl.gm_d;
+            Acc<double> acc;
+            acc.reset();
+            for (int q = q0 + rw; q < q1; q += nrw) {
+                const int i = 32 * q + lane;
+                const int off = s_pre[q] - e_base + lane;
+                const int L = (s_pre[q + 1] - s_pre[q]) >> 5;
+                const double xi = (i < n) ? x[i] : 0.0;
+                double a0 = 0.0, a1 = 0.0;
+                int k = 0;
+                for (; k + 1 < L; k += 2) {
+                    a0 = fma(s_w[off + 32 * k], x[s_col[off + 32 * k]], a0);
+                    a1 = fma(s_w[off + 32 * k + 32], x[s_col[off + 32 * k + 32]], a1);
+                }
+                if (k < L) a0 = fma(s_w[off + 32 * k], x[s_col[off + 32 * k]], a0);
+                if (i < n) {
+                    const double yv = (fma(s_gd[i], xi, a0 + a1) - gm) * sig;
+                    y[i] = yv;
+                    for (int r = 0; r < C; r++)
+                        if (r != (int)rank) st_cluster_f64(&y[i], (unsigned)r, yv);
+                    acc.add(yv, xi);
+                }
+            }
+            double *dst = s_dacc + ((size_t)((s + 1) & 1) * blockDim.x + tid) * 3;
+            dst[0] = acc.A;
+            dst[1] = acc.B;
+            dst[2] = acc.C;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            // this CTA's totals of the sweep (row warps in order per lane,
+            // then the lanes' xor tree), stored into every CTA's slot
+            double A = 0.0, B = 0.0, Cc = 0.0;
+            for (int w = 1; w < nw; w++) {
+                const double *src = s_dacc + ((size_t)((s + 1) & 1) * blockDim.x + 32 * w + lane) * 3;
+                A += src[0];
+                B += src[1];
+                Cc += src[2];
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                A += __shfl_xor_sync(0xffffffffu, A, o);
+                B += __shfl_xor_sync(0xffffffffu, B, o);
+                Cc += __shfl_xor_sync(0xffffffffu, Cc, o);
+            }
+            if (lane < C) {
+                double *slot = s_part + ((size_t)(s & 1) * kClusterMax + rank) * 3;
+                if (lane == (int)rank) {
+                    slot[0] = A;
+                    slot[1] = B;
+                    slot[2] = Cc;
+                } else {
+                    st_cluster_f64(slot + 0, (unsigned)lane, A);
+                    st_cluster_f64(slot + 1, (unsigned)lane, B);
+                    st_cluster_f64(slot + 2, (unsigned)lane, Cc);
+                }
+            }
+        }
+        cluster_barrier();
+        s++;
+    }
+    __shared__ int s_rb, s_rbp;
+    if (warp == 0) {
+        if (exit_kind == 2 && !no_sweeps) {
+            const Part q = cluster_part((s - 1) & 1);
+            ctrl_step(a, s, q, c, nullptr, true, true);
+        }
+        if (lane == 0) {
+            const int rs = c.res_sweep;
+            s_rb = c.zero ? (rs + 2) % 3 : rs % 3;
+            s_rbp = (rs + 2) % 3;
+            if (rank == 0) write_result(a, c, 0, 1);
+        }
+    }
+    __syncthreads();
+    if (rank == 0) {
+        // result -> buf[0], previous iterate -> buf[1]
+        double *o0 = (double *)a.buf[0], *o1 = (double *)a.buf[1];
+        const double *rr = ring0 + (size_t)s_rb * n, *rp = ring0 + (size_t)s_rbp * n;
+        for (int i = tid; i < n; i += blockDim.x) {
+            o0[i] = rr[i];
+            o1[i] = rp[i];
+        }
+    }
+}
+
+static size_t cluster_smem(int n, int threads, int emax) {
+    const int nsl = (n + 31) / 32;
+    return 8 * (4 * (size_t)n + 2 * kClusterMax * 3 + 2 * (size_t)threads * 3 + (size_t)emax) +
+           4 * ((size_t)emax + nsl + 1) + 16;
+}
+
+void cluster_plan(PiLevel *lv, const int *rph) {
+    lv->cl_ctas = 0;
+    const int n = lv->n;
+    if (n < kClusterMinRows || n > 65536) return;
+    DeviceInfo d;
+    if (device_info(&d) != CMG_OK) return;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)k_power_cluster) != cudaSuccess) return;
+    const long long room = (long long)d.max_smem_optin - (long long)fa.sharedSizeBytes - 1024;
+    const int nsl = (n + 31) / 32;
+    std::vector<int> pre(nsl + 1, 0);
+    for (int q = 0; q < nsl; q++) {
+        int L = 0;
+        for (int r = 32 * q; r < std::min(n, 32 * q + 32); r++) L = std::max(L, rph[r + 1] - rph[r]);
+        pre[q + 1] = pre[q] + 32 * L;
+    }
+    // about 96 rows per CTA: enough FP64 work per SM to repay the barrier
+    for (int C = std::max(2, std::min(kClusterMax, (n + 95) / 96)); C <= kClusterMax; C++) {
+        int emax = 0, smax = 0;
+        for (int r = 0; r < C; r++) {
+            const int a0 = cluster_split(pre.data(), nsl, C, r), a1 = cluster_split(pre.data(), nsl, C, r + 1);
+            emax = std::max(emax, pre[a1] - pre[a0]);
+            smax = std::max(smax, a1 - a0);
+        }
+        const int threads = 32 * (1 + std::max(1, std::min(31, smax)));
+        const size_t smem = cluster_smem(n, threads, emax);
+        if ((long long)smem > room) continue;
+        if (allow_max_dynamic_smem((const void *)k_power_cluster) != CMG_OK) return;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)C);
+        cfg.blockDim = dim3((unsigned)threads);
+        cfg.dynamicSmemBytes = smem;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int ncl = 0;
+        if (cudaOccupancyMaxActiveClusters(&ncl, (const void *)k_power_cluster, &cfg) != cudaSuccess || ncl < 1) {
+            cudaGetLastError();
+            return;
+        }
+        lv->cl_ctas = C;
+        lv->cl_threads = threads;
+        lv->cl_emax = emax;
+        lv->cl_smem = smem;
+        return;
+    }
+}
+
 // ================================================================== host side
 __global__ void k_tiles(int n, const int *__restrict__ rp, int ntiles, int *__restrict__ tile_row) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k <= ntiles; k += gridDim.x * blockDim.x) {
@@ -1672,12 +2008,15 @@ int stage_capacity(int fp32) {
     return (int)(cap & ~3ll);
 }
 
-bool small_level_fits(const PiLevel &lv, int fp32) {
+// Lanes per row with which the small kernel holds the level (0: it cannot).
+static int small_config(const PiLevel &lv, int fp32) {
     DeviceInfo d;
-    if (device_info(&d) != CMG_OK) return false;
+    if (device_info(&d) != CMG_OK) return 0;
     const int G = small_lanes(lv.n, lv.nnz, fp32);
-    return small_bytes(lv, G, fp32) + 4096 <= (size_t)d.max_smem_optin;
+    return small_bytes(lv, G, fp32) + 4096 <= (size_t)d.max_smem_optin ? G : 0;
 }
+
+bool small_level_fits(const PiLevel &lv, int fp32) { return small_config(lv, fp32) > 0; }
 
 __global__ void k_sell_size(int n_static, const int *__restrict__ n_dev, const int *__restrict__ rp,
                             unsigned long long *out) {
@@ -1753,8 +2092,27 @@ cmg_status_t power_iteration(const PiRun &run, GridSync *gs, cudaStream_t s, con
     a.stream_hint = 0;
     a.stage_n = 0;
     void *args[] = {&a, &gs};
+    if (lv.cl_ctas > 0 && !run.fp32 && !lv.lay) {
+        // FP64 sweeps in one thread-block cluster
+        a.cl_emax = lv.cl_emax;
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = (unsigned)lv.cl_ctas;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)lv.cl_ctas);
+        cfg.blockDim = dim3((unsigned)lv.cl_threads);
+        cfg.dynamicSmemBytes = lv.cl_smem;
+        cfg.stream = s;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        CMG_TRY(allow_max_dynamic_smem((const void *)k_power_cluster));
+        CMG_CUDA(cudaLaunchKernelExC(&cfg, (const void *)k_power_cluster, args));
+        return launch_status();
+    }
     if (small_level_fits(lv, run.fp32)) {
-        const int G = small_lanes(lv.n, lv.nnz, run.fp32);
+        const int G = small_config(lv, run.fp32);
         const void *kern = run.fp32 ? small_kernel<float>(G) : small_kernel<double>(G);
         const size_t smem = small_bytes(lv, G, run.fp32);
         CMG_TRY(allow_max_dynamic_smem(kern));

@@ -62,7 +62,7 @@ def test_two_phase_fp64_matches_oracle(monkeypatch, name, knobs):
     h = cmg.Hierarchy(rp, col, w, seed=1412)
     kind, _ = h.level_kernels()
     assert KIND_TWO_PHASE in kind
-    assert all(k in (0, KIND_TWO_PHASE) for k in kind)
+    assert all(k in (0, KIND_TWO_PHASE, 5) for k in kind)   # 5: cluster kernel on small FP64 levels
     u, lam, st = h.fiedler()
     u2, lam2, _ = h.fiedler()
     h.close()
