@@ -382,10 +382,13 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     }
     // ---- FP64 levels of 512 to a few thousand rows: sweeps in one thread-
     // block cluster (every CTA holds the iterate; rows split over the SMs)
-    if (!getenv("CMG_CLUSTER") || getenv("CMG_CLUSTER")[0] != '0') {
+    // (CMG_CLUSTER=0: never; CMG_CLUSTER=<rows>: from that many rows on)
+    const char *cl_env = getenv("CMG_CLUSTER");
+    if (!cl_env || cl_env[0] != '0') {
+        const int cl_min = cl_env ? std::max(128, atoi(cl_env)) : 512;
         std::vector<int> rph;
         for (auto &L : h->lv) {
-            if (L.fp32 || L.n < 512 || L.n > 65536) continue;
+            if (L.fp32 || L.n < cl_min || L.n > 65536) continue;
             rph.resize((size_t)L.n + 1);
             CMG_CUDA(cudaMemcpyAsync(rph.data(), L.rp, sizeof(int) * ((size_t)L.n + 1), cudaMemcpyDeviceToHost, s));
             CMG_CUDA(cudaStreamSynchronize(s));

@@ -53,9 +53,17 @@ __device__ long long g_x2t[160][32][8];
 extern "C" int cmg_debug_x2_trace(long long *host, int count) {
     return (int)cudaMemcpyFromSymbol(host, g_x2t, sizeof(long long) * (size_t)count);
 }
+// cycle stamps of the cluster kernel's first sweeps (rank 0, thread 0):
+// [s][0] loop top, [1] rows done, [2] sums stored, [3] after the barrier
+__device__ long long g_clt[256][4];
+#define CLT(s, k) do { if ((s) < 256 && threadIdx.x == 0 && cluster_rank() == 0) g_clt[(s)][(k)] = clock64(); } while (0)
+extern "C" int cmg_debug_cluster_trace(long long *host, int count) {
+    return (int)cudaMemcpyFromSymbol(host, g_clt, sizeof(long long) * (size_t)count);
+}
 #else
 #define TRACE(s, k) do { } while (0)
 #define X2T(s, t, k) do { } while (0)
+#define CLT(s, k) do { } while (0)
 #endif
 
 // Loads of data written by other CTAs of the same launch go through L2.
@@ -1544,22 +1552,20 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
 
 // ================================================================== cluster kernel
 // FP64 sweeps of a level spread over one thread-block cluster of C CTAs
-// (2..8, one per SM).  Every CTA holds the whole iterate ring (3 n doubles)
-// and g - d_i of every row, and the SELL-32 slices of its share of the rows
-// (slices split into C ranges of about equal SELL size).  A sweep: the row
-// warps compute their rows from the local iterate and store each y_i into
-// every CTA's ring (distributed shared memory); the control warp sums the
-// CTA's stop sums (fixed order) and stores the three totals into every CTA's
-// slot [sweep parity][rank]; then the cluster meets at its barrier.  Every
+// (2..8, one per SM).  Every CTA holds the whole iterate ring (3 x n rows
+// rounded up to whole slices) and g - d_i of every row, and the SELL-32
+// slices of its share of the rows (slices split into C ranges of about
+// equal SELL size).  A sweep: the row warps compute their rows from the
+// local iterate (each warp's stop sums summed over its lanes as float-
+// float); then all threads copy the CTA's row block, in 16-byte pieces, into
+// every other CTA's ring (distributed shared memory) while the control warp
+// sums the warps' stop sums and stores the total into every CTA's slot
+// [sweep parity][rank]; then the cluster meets at its barrier.  Every
 // CTA's control warp sums the C slots in rank order and takes the same
 // decisions, so all CTAs run the same sweeps and reach the same barriers.
 // A CTA is at most one sweep ahead of another (one barrier per sweep), so
 // two slot parities and the ring of three keep stores and reads apart.
 constexpr int kClusterMax = 8;
-// Below this many rows one CTA's sweep (the one-CTA kernel) is faster: the
-// cluster's per-sweep barrier and exchange cost more than the FP64 work it
-// spreads (measured: 245 rows, 3.5 against 2.7 us per sweep).
-constexpr int kClusterMinRows = 512;
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -1576,11 +1582,18 @@ __device__ __forceinline__ unsigned cluster_ctas() {
 __device__ __forceinline__ void cluster_barrier() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void st_cluster_f64(double *local, unsigned cta, double v) {
+__device__ __forceinline__ unsigned cluster_addr(const void *local, unsigned cta) {
     const unsigned la = (unsigned)__cvta_generic_to_shared(local);
     unsigned ra;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(la), "r"(cta));
-    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(ra), "d"(v) : "memory");
+    return ra;
+}
+__device__ __forceinline__ void st_cluster_f32(float *local, unsigned cta, float v) {
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(cluster_addr(local, cta)), "f"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_v2f64(double2 *local, unsigned cta, double2 v) {
+    asm volatile("st.shared::cluster.v2.f64 [%0], {%1, %2};" ::"r"(cluster_addr(local, cta)), "d"(v.x), "d"(v.y)
+                 : "memory");
 }
 
 // First slice of each of C ranges of about equal SELL-32 size, from the
@@ -1601,18 +1614,17 @@ __host__ __device__ __forceinline__ int cluster_split(const int *pre, int nsl, i
 
 __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, GridSync *) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int n = a.n, nsl = (n + 31) / 32;
+    const int n = a.n, nsl = (n + 31) / 32, nr = 32 * nsl;   // ring slots hold whole slices
     const int C = (int)cluster_ctas();
     const unsigned rank = cluster_rank();
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nw = blockDim.x >> 5, nrw = nw - 1, rw = warp - 1;
-    double *ring0 = reinterpret_cast<double *>(smem_raw);
-    double *s_gd = ring0 + 3 * (size_t)n;
-    double *s_part = s_gd + n;                            // [2][kClusterMax][3]
-    double *s_dacc = s_part + 2 * kClusterMax * 3;        // [2][blockDim][3]
-    double *s_w = s_dacc + 2 * (size_t)blockDim.x * 3;    // [emax]
+    double *ring0 = reinterpret_cast<double *>(smem_raw);      // [3][nr]
+    double *s_gd = ring0 + 3 * (size_t)nr;                      // [nr]
+    Part *s_cpart = reinterpret_cast<Part *>(s_gd + nr);        // [2][kClusterMax]: CTAs' stop sums
+    double *s_w = reinterpret_cast<double *>(s_cpart + 2 * kClusterMax);   // [emax]
     int *s_col = reinterpret_cast<int *>(s_w + a.cl_emax);
-    int *s_pre = s_col + a.cl_emax;                       // [nsl + 1]
+    int *s_pre = s_col + a.cl_emax;                             // [nsl + 1]
     __shared__ Part s_pw[32];
     __shared__ Slot s_slot[2];
     __shared__ int s_q[2];
@@ -1649,7 +1661,6 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
             }
         }
     }
-    for (int k = tid; k < 2 * kClusterMax * 3; k += blockDim.x) s_part[k] = 0.0;
     // ---- start vector and g - d_i of every row (the same in every CTA)
     {
         const void *cb = nullptr;
@@ -1660,15 +1671,21 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
             cinv = a.cres->inv_s;
         }
         Part acc = part_zero();
-        for (int i = tid; i < n; i += blockDim.x) {
-            const double xt = start_value(a, i, cb, cmu, cinv);
+        for (int i = tid; i < nr; i += blockDim.x) {
+            double xt = 0.0, gd = 0.0;
+            if (i < n) {
+                xt = start_value(a, i, cb, cmu, cinv);
+                double d = 0.0;
+                for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
+                gd = g - d;
+                const ff v = ff_from_double(xt);
+                acc.A = ff_add(acc.A, v);
+                acc.B = ff_add(acc.B, ff_mul(v, v));
+            }
             ring0[i] = xt;
-            double d = 0.0;
-            for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
-            s_gd[i] = g - d;
-            const ff v = ff_from_double(xt);
-            acc.A = ff_add(acc.A, v);
-            acc.B = ff_add(acc.B, ff_mul(v, v));
+            ring0[nr + i] = 0.0;
+            ring0[2 * (size_t)nr + i] = 0.0;
+            s_gd[i] = gd;
         }
         Part p = warp_sum_part(acc);
         if (lane == 0) s_pw[warp] = p;
@@ -1692,23 +1709,14 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
     // every CTA's shared memory is set up before any CTA stores into it
     cluster_barrier();
 
-    // the C CTAs' totals of parity par, summed in rank order (lane 0), then
-    // given to every lane of the control warp
+    // the C CTAs' stop sums of parity par, in rank order (every lane)
     auto cluster_part = [&](int par) -> Part {
-        double A = 0.0, B = 0.0, Cc = 0.0;
-        if (lane == 0)
-            for (int r = 0; r < C; r++) {
-                const double *src = s_part + ((size_t)par * kClusterMax + r) * 3;
-                A += src[0];
-                B += src[1];
-                Cc += src[2];
-            }
-        Part p;
-        p.A = ff_from_double(__shfl_sync(0xffffffffu, A, 0));
-        p.B = ff_from_double(__shfl_sync(0xffffffffu, B, 0));
-        p.C = ff_from_double(__shfl_sync(0xffffffffu, Cc, 0));
-        return p;
+        Part q = part_zero();
+        for (int r = 0; r < C; r++) q = part_add(q, s_cpart[par * kClusterMax + r]);
+        return q;
     };
+    // this CTA's row block, in 16-byte pieces, into every other CTA's ring
+    const int rb0 = 32 * q0, rb_pairs = 16 * (q1 - q0);
 
     const bool no_sweeps = (a.mode == 1 && a.k_fixed <= 0);
     int s = 0;
@@ -1723,8 +1731,9 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
             exit_kind = 2;
             break;
         }
-        const double *x = ring0 + (size_t)(s % 3) * n;
-        double *y = ring0 + (size_t)((s + 1) % 3) * n;
+        const double *x = ring0 + (size_t)(s % 3) * nr;
+        double *y = ring0 + (size_t)((s + 1) % 3) * nr;
+        CLT(s, 0);
         if (warp == 0) {
             if (s >= 1) {
                 const Part q = cluster_part((s - 1) & 1);
@@ -1740,7 +1749,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
                 const int i = 32 * q + lane;
                 const int off = s_pre[q] - e_base + lane;
                 const int L = (s_pre[q + 1] - s_pre[q]) >> 5;
-                const double xi = (i < n) ? x[i] : 0.0;
+                const double xi = x[i];
                 double a0 = 0.0, a1 = 0.0;
                 int k = 0;
                 for (; k + 1 < L; k += 2) {
@@ -1751,47 +1760,39 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
                 if (i < n) {
                     const double yv = (fma(s_gd[i], xi, a0 + a1) - gm) * sig;
                     y[i] = yv;
-                    for (int r = 0; r < C; r++)
-                        if (r != (int)rank) st_cluster_f64(&y[i], (unsigned)r, yv);
                     acc.add(yv, xi);
                 }
             }
-            double *dst = s_dacc + ((size_t)((s + 1) & 1) * blockDim.x + tid) * 3;
-            dst[0] = acc.A;
-            dst[1] = acc.B;
-            dst[2] = acc.C;
+            // the warp's stop sums as float-float, summed over its lanes
+            const Part p = warp_sum_part(acc.get());
+            if (lane == 0) s_pw[warp] = p;
         }
         __syncthreads();
+        CLT(s, 1);
         if (warp == 0) {
-            // this CTA's totals of the sweep (row warps in order per lane,
-            // then the lanes' xor tree), stored into every CTA's slot
-            double A = 0.0, B = 0.0, Cc = 0.0;
-            for (int w = 1; w < nw; w++) {
-                const double *src = s_dacc + ((size_t)((s + 1) & 1) * blockDim.x + 32 * w + lane) * 3;
-                A += src[0];
-                B += src[1];
-                Cc += src[2];
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                A += __shfl_xor_sync(0xffffffffu, A, o);
-                B += __shfl_xor_sync(0xffffffffu, B, o);
-                Cc += __shfl_xor_sync(0xffffffffu, Cc, o);
-            }
+            // this CTA's stop sums (row warps in order) into every CTA's slot
+            Part q = (lane >= 1 && lane < nw) ? s_pw[lane] : part_zero();
+            q = warp_sum_part(q);
             if (lane < C) {
-                double *slot = s_part + ((size_t)(s & 1) * kClusterMax + rank) * 3;
+                Part *slot = s_cpart + (s & 1) * kClusterMax + rank;
                 if (lane == (int)rank) {
-                    slot[0] = A;
-                    slot[1] = B;
-                    slot[2] = Cc;
+                    *slot = q;
                 } else {
-                    st_cluster_f64(slot + 0, (unsigned)lane, A);
-                    st_cluster_f64(slot + 1, (unsigned)lane, B);
-                    st_cluster_f64(slot + 2, (unsigned)lane, Cc);
+                    const float *src = reinterpret_cast<const float *>(&q);
+                    float *dst = reinterpret_cast<float *>(slot);
+                    for (int k = 0; k < 6; k++) st_cluster_f32(dst + k, (unsigned)lane, src[k]);
                 }
             }
         }
+        for (int k = tid; k < (C - 1) * rb_pairs; k += blockDim.x) {
+            const int pr = k / rb_pairs, j = k - pr * rb_pairs;
+            const unsigned peer = (unsigned)(pr < (int)rank ? pr : pr + 1);
+            const double2 v = reinterpret_cast<const double2 *>(y + rb0)[j];
+            st_cluster_v2f64(reinterpret_cast<double2 *>(y + rb0) + j, peer, v);
+        }
+        CLT(s, 2);
         cluster_barrier();
+        CLT(s, 3);
         s++;
     }
     __shared__ int s_rb, s_rbp;
@@ -1811,7 +1812,7 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
     if (rank == 0) {
         // result -> buf[0], previous iterate -> buf[1]
         double *o0 = (double *)a.buf[0], *o1 = (double *)a.buf[1];
-        const double *rr = ring0 + (size_t)s_rb * n, *rp = ring0 + (size_t)s_rbp * n;
+        const double *rr = ring0 + (size_t)s_rb * nr, *rp = ring0 + (size_t)s_rbp * nr;
         for (int i = tid; i < n; i += blockDim.x) {
             o0[i] = rr[i];
             o1[i] = rp[i];
@@ -1819,16 +1820,15 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
     }
 }
 
-static size_t cluster_smem(int n, int threads, int emax) {
-    const int nsl = (n + 31) / 32;
-    return 8 * (4 * (size_t)n + 2 * kClusterMax * 3 + 2 * (size_t)threads * 3 + (size_t)emax) +
-           4 * ((size_t)emax + nsl + 1) + 16;
+static size_t cluster_smem(int n, int, int emax) {
+    const int nsl = (n + 31) / 32, nr = 32 * nsl;
+    return 8 * (4 * (size_t)nr + (size_t)emax) + sizeof(Part) * 2 * kClusterMax + 4 * ((size_t)emax + nsl + 1) + 16;
 }
 
 void cluster_plan(PiLevel *lv, const int *rph) {
     lv->cl_ctas = 0;
     const int n = lv->n;
-    if (n < kClusterMinRows || n > 65536) return;
+    if (n < 128 || n > 65536) return;
     DeviceInfo d;
     if (device_info(&d) != CMG_OK) return;
     cudaFuncAttributes fa;
