@@ -98,10 +98,39 @@ __global__ void k_scan_down(const int *__restrict__ in, int *__restrict__ out, i
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
 }
 
+// One CTA of 1024 threads, 8 consecutive items each: the whole scan of up to
+// kScanSmall items in one launch (setup scans many short arrays, where the
+// three launches of the tiled scan cost more than the work).
+constexpr int kScanSmall = 8192;
+__global__ void __launch_bounds__(1024) k_scan_small(const int *__restrict__ in, int *__restrict__ out, int n) {
+    __shared__ int sm[32];
+    int v[8];
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int i = threadIdx.x * 8 + k;
+        v[k] = (i < n) ? in[i] : 0;
+        t += v[k];
+    }
+    int tot;
+    int run = block_scan_excl(t, sm, &tot);
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const int i = threadIdx.x * 8 + k;
+        if (i < n) out[i] = run;
+        run += v[k];
+    }
+    if (threadIdx.x == 0) out[n] = tot;
+}
+
 cmg_status_t exclusive_scan(const int *in, int *out, int n, Scratch &scr, cudaStream_t s) {
     if (n <= 0) {
         CMG_CUDA(cudaMemsetAsync(out, 0, sizeof(int), s));
         return CMG_OK;
+    }
+    if (n <= kScanSmall) {
+        k_scan_small<<<1, 1024, 0, s>>>(in, out, n);
+        return launch_status();
     }
     const int nb = div_up(n, kScanTile);
     int *part;
