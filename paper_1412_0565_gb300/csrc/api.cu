@@ -402,13 +402,13 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     }
     // ---- sweep layouts for the levels the shared-memory kernels cannot hold
     size_t lay_bytes = 0;
-    std::vector<int> stage_try(nlev, 0);
-    std::vector<unsigned long long> below(nlev, 0);
+    std::vector<int> stage_try(nlev, 0), partial_try(nlev, 0);
+    std::vector<unsigned long long> below(2 * (size_t)nlev, 0);
     unsigned long long *below_dev = nullptr;
     {
         int *voff1;
         CMG_TRY(scr.get(&voff1, 2));
-        CMG_TRY(scr.get(&below_dev, (size_t)nlev));
+        CMG_TRY(scr.get(&below_dev, 2 * (size_t)nlev));
         for (int k = 0; k < nlev; k++) {
             LevelData &L = h->lv[k];
             if (L.cl_ctas > 0 || small_level_fits(level_view(L), L.fp32)) continue;
@@ -439,6 +439,10 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
             // gathers that a staged prefix of the iterate would serve
             stage_try[k] = std::min(L.n, stage_capacity(L.fp32));
             if (stage_try[k] > 0) CMG_TRY(layout_count_below(L.lay, stage_try[k], below_dev + k, s));
+            if (L.fp32 && stage_try[k] > kPartialStage) {
+                partial_try[k] = kPartialStage;
+                CMG_TRY(layout_count_below(L.lay, kPartialStage, below_dev + nlev + k, s));
+            }
         }
     }
     // ---- solve workspace: an iterate ring per level, results, barrier state
@@ -471,19 +475,25 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
     bool any_stage = false;
     for (int k = 0; k < nlev; k++) any_stage = any_stage || stage_try[k] > 0;
     if (any_stage)
-        CMG_CUDA(cudaMemcpyAsync(below.data(), below_dev, sizeof(unsigned long long) * (size_t)nlev,
+        CMG_CUDA(cudaMemcpyAsync(below.data(), below_dev, sizeof(unsigned long long) * 2 * (size_t)nlev,
                                  cudaMemcpyDeviceToHost, s));
     CMG_CUDA(cudaStreamSynchronize(s));
     if (any_stage) {
         // CMG_STAGE=0: never stage the iterate; CMG_STAGE=1: stage it on every
-        // level with a sweep layout; otherwise where stage_pays() says so
+        // level with a sweep layout; otherwise where stage_pays() says so, or
+        // a short prefix where partial_stage_pays() does (FP32 sweeps)
         const char *env = getenv("CMG_STAGE");
         const int mode = (env && env[0] == '0') ? 0 : ((env && env[0] == '1') ? 1 : 2);
         DeviceInfo di;
         CMG_TRY(device_info(&di));
-        for (int k = 0; k < nlev; k++)
-            if (stage_try[k] > 0 && (mode == 1 || (mode == 2 && stage_pays(below[k], h->lv[k].lay.entries, di.sms))))
+        for (int k = 0; k < nlev; k++) {
+            const LevelData &L = h->lv[k];
+            if (stage_try[k] > 0 && (mode == 1 || (mode == 2 && stage_pays(below[k], L.lay.entries, di.sms))))
                 h->lv[k].lay.stage_n = stage_try[k];
+            else if (mode == 2 && partial_try[k] > 0 &&
+                     partial_stage_pays(below[nlev + k], L.lay.entries, L.n, di.sms))
+                h->lv[k].lay.stage_n = partial_try[k];
+        }
     }
     return CMG_OK;
 }

@@ -167,6 +167,16 @@ int stage_capacity(int fp32);
 inline bool stage_pays(unsigned long long below, long long entries, int sms) {
     return entries >= 16384ll * sms && below * 10ull >= (unsigned long long)entries * 9ull;
 }
+// FP32 sweeps of a level the rule above leaves unstaged: a short prefix of
+// kPartialStage entries leaves most of L1 to the other gathers and pays when
+// it serves at least 3 times its share of the rows (`below` of `entries`
+// gathers for kPartialStage of n rows): the hub columns of a power-law
+// level, not the even columns of a grid level.
+constexpr int kPartialStage = 32768;
+inline bool partial_stage_pays(unsigned long long below, long long entries, int n, int sms) {
+    return entries >= 16384ll * sms && n > 2 * kPartialStage &&
+           (double)below * (double)n >= 3.0 * (double)kPartialStage * (double)entries;
+}
 
 // Bits needed for the ids 0..c-1 (at least 1).
 inline int bits_for(int c) {

@@ -225,12 +225,15 @@ def test_staged_iterate_kernel_matches_oracle(monkeypatch, precision):
 def test_stage_rule_picks_dense_power_law_levels():
     """Without the override, staging is chosen where gathers are many per
     staged entry: the dense coarse levels of a power-law graph, not the
-    levels of a 3-D grid."""
+    levels of a 3-D grid.  A level whose iterate is far longer than shared
+    memory stages a 32,768-entry prefix in the FP32 form when that prefix
+    serves at least 3 times its share of the rows (the hub columns: 42 % of
+    level 0's gathers for 8.2 % of its rows here)."""
     # levels of this graph: 399,708 / 105,389 / 25,604 / 6,072 / 1,088 rows
     # with 6.4M / 5.7M / 5.3M / 3.8M / 0.65M stored entries
     h = cmg.Hierarchy(*inputs.chung_lu(400000, seed=12), seed=1412, precision="fp32")
     kind, staged = h.level_kernels()
-    assert kind[0] == 1 and staged[0] == 0       # a short prefix of a long iterate
+    assert kind[0] == 2 and staged[0] == 32768   # a short prefix of a long iterate
     assert kind[2] == 2 and staged[2] == 25604   # the whole iterate, 5.3M gathers a sweep
     h.close()
     h = cmg.Hierarchy(*inputs.grid3d(60, 60, 60, "uniform", seed=1), seed=1412, precision="fp32")
