@@ -388,7 +388,7 @@ static cmg_status_t build_hierarchy(cmg_hierarchy_s *h, int64_t n, const int64_t
         const int cl_min = cl_env ? std::max(128, atoi(cl_env)) : 512;
         std::vector<int> rph;
         for (auto &L : h->lv) {
-            if (L.fp32 || L.n < cl_min || L.n > 65536) continue;
+            if (L.fp32 || L.n < cl_min || !cluster_may_hold(L.n)) continue;
             rph.resize((size_t)L.n + 1);
             CMG_CUDA(cudaMemcpyAsync(rph.data(), L.rp, sizeof(int) * ((size_t)L.n + 1), cudaMemcpyDeviceToHost, s));
             CMG_CUDA(cudaStreamSynchronize(s));

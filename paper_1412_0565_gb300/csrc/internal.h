@@ -254,6 +254,10 @@ struct PiLevel {
 // lv->cl_ctas at 0 when the level is outside the plan's range or no cluster
 // of that size can be resident.
 void cluster_plan(PiLevel *lv, const int *rp_host);
+// Whether a cluster CTA could hold an n-row level's iterate ring (3 x n
+// values), g - d_i and slot order at all: the check before cluster_plan,
+// which needs the level's row pointers on the host.
+bool cluster_may_hold(int n);
 
 // SELL-32 size of a CSR level (sum over 32-row slices of 32 x longest row);
 // dev_counter: one device unsigned long long of scratch.  Synchronises s.

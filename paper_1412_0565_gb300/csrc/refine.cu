@@ -32,6 +32,7 @@
 //   k_power_small  small levels: one CTA holds the CSR and the iterate ring in
 //                  shared memory; one __syncthreads per sweep.
 #include <algorithm>
+#include <functional>
 #include <math.h>
 
 #include "ffloat.cuh"
@@ -1273,10 +1274,154 @@ __global__ void __launch_bounds__(kStageThreads, 1) k_power_2p(PiArgs a, GridSyn
 // size (one lane per row: each 32-row slice stores entry k of its rows
 // contiguously, rows padded to the slice's longest with zero weights, so the
 // lanes of a warp read consecutive words -- no bank conflicts).
+// ================================================================== slot order
+// The one-CTA and cluster kernels hold a level's rows in "slot" order: rows by
+// decreasing degree, ties by row number, so that the 32 rows of a SELL-32
+// slice have about the same length and the slices carry little padding (a
+// padded entry costs an FP64 FMA like a stored one).  The iterate, g - d_i
+// and the columns are renumbered to slots; rows are mapped back on output.
+// The order is taken when it shrinks the SELL-32 size by at least 1/16 and
+// every row holds fewer than n entries; otherwise slots are rows.  Sorted
+// order never needs more entries than row order: in any order, at least k+1
+// slices hold a row at least as long as the sorted row at position 32k, so
+// the k-th widest slice is at least as wide as the sorted order's k-th slice,
+// and a buffer sized for row order holds either.
+__host__ __device__ __forceinline__ bool slot_order_pays(long long natural, long long sorted) {
+    return sorted * 16 <= natural * 15;
+}
+
+// perm[p] = row of slot p and inv[i] = slot of row i (n ints each, shared
+// memory); hist: n ints of shared scratch.  A stable counting sort: bucket
+// maxdeg - d_i, bucket starts by one warp's scan, rows placed by one warp in
+// row order (rows of equal degree keep their order).  Every thread of the CTA
+// calls it; the CTA is synchronised on return.
+__device__ __noinline__ void slot_order(int n, const int *rp, int *perm, int *inv, int *hist) {
+    __shared__ int s_maxd, s_sorted;
+    __shared__ unsigned long long s_nat;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+    if (tid == 0) {
+        s_maxd = 0;
+        s_sorted = 0;
+        s_nat = 0;
+    }
+    __syncthreads();
+    int md = 0;
+    unsigned long long nat = 0;
+    for (int i = tid; i < n; i += nt) md = max(md, rp[i + 1] - rp[i]);
+    for (int q = tid; q < (n + 31) / 32; q += nt) {
+        int L = 0;
+        for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, rp[r + 1] - rp[r]);
+        nat += 32ull * (unsigned long long)L;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        md = max(md, __shfl_xor_sync(0xffffffffu, md, o));
+        nat += __shfl_xor_sync(0xffffffffu, nat, o);
+    }
+    if (lane == 0) {
+        atomicMax(&s_maxd, md);
+        atomicAdd(&s_nat, nat);
+    }
+    __syncthreads();
+    const int D = s_maxd;
+    if (D < n) {
+        for (int b = tid; b <= D; b += nt) hist[b] = 0;
+        __syncthreads();
+        for (int i = tid; i < n; i += nt) {
+            const int b = D - (rp[i + 1] - rp[i]);
+            inv[i] = b;   // the row's bucket, read back by the placing warp
+            atomicAdd(&hist[b], 1);
+        }
+        __syncthreads();
+        if (tid < 32) {
+            // bucket starts (exclusive scan) and the SELL-32 size in slot
+            // order: a slice is as wide as the degree of its first slot
+            int carry = 0;
+            unsigned long long tot = 0;
+            for (int b0 = 0; b0 <= D; b0 += 32) {
+                const int b = b0 + lane;
+                const int c = (b <= D) ? hist[b] : 0;
+                int incl = c;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                const int st = carry + incl - c;
+                if (b <= D) {
+                    hist[b] = st;
+                    const int starts = (st + c + 31) / 32 - (st + 31) / 32;
+                    tot += 32ull * (unsigned long long)(D - b) * (unsigned long long)starts;
+                }
+                carry += __shfl_sync(0xffffffffu, incl, 31);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+            if (lane == 0) s_sorted = slot_order_pays((long long)s_nat, (long long)tot) ? 1 : 0;
+        }
+        __syncthreads();
+    }
+    if (s_sorted) {
+        if (tid < 32) {
+            for (int i0 = 0; i0 < n; i0 += 32) {
+                const int i = i0 + lane;
+                const unsigned act = __ballot_sync(0xffffffffu, i < n);
+                if (i < n) {
+                    const int b = inv[i];
+                    const unsigned peers = __match_any_sync(act, b);
+                    const int r = __popc(peers & ((1u << lane) - 1u));
+                    const int base = hist[b];
+                    perm[base + r] = i;
+                    __syncwarp(act);
+                    if (r == 0) hist[b] = base + __popc(peers);
+                }
+                __syncwarp();
+            }
+        }
+    } else {
+        for (int p = tid; p < n; p += nt) perm[p] = p;
+    }
+    __syncthreads();
+    for (int p = tid; p < n; p += nt) inv[perm[p]] = p;
+    __syncthreads();
+}
+
+// Prefix sums pre[0..nsl] of the SELL-32 slice sizes in the order slot_order
+// takes, from the host copy of the row pointers (the same arithmetic; the
+// sorted widths come from the degree counts: slice q of the sorted rows is as
+// wide as the degree at sorted position 32q).
+static void slot_sell_prefix(int n, const int *rph, std::vector<int> &pre) {
+    const int nsl = (n + 31) / 32;
+    std::vector<int> wid(nsl, 0);
+    int D = 0;
+    long long nat = 0;
+    for (int q = 0; q < nsl; q++) {
+        for (int r = 32 * q; r < std::min(n, 32 * q + 32); r++) wid[q] = std::max(wid[q], rph[r + 1] - rph[r]);
+        nat += 32ll * wid[q];
+        D = std::max(D, wid[q]);
+    }
+    if (D < n) {
+        std::vector<int> cnt((size_t)D + 1, 0), sw(nsl, 0);
+        for (int i = 0; i < n; i++) cnt[rph[i + 1] - rph[i]]++;
+        long long tot = 0;
+        int pos = 0;   // sorted position of the first row of degree d
+        for (int d = D; d >= 0; d--) {
+            for (int q = (pos + 31) / 32; 32 * q < pos + cnt[d]; q++) {
+                sw[q] = d;
+                tot += 32ll * d;
+            }
+            pos += cnt[d];
+        }
+        if (slot_order_pays(nat, tot)) wid.swap(sw);
+    }
+    pre.assign(nsl + 1, 0);
+    for (int q = 0; q < nsl; q++) pre[q + 1] = pre[q] + 32 * wid[q];
+}
+
 template <typename T>
 constexpr size_t small_smem_bytes(long long n, long long e) {
     return (size_t)(sizeof(T) * (3 * n + e) + (sizeof(T) == 8 ? 8 * n : 0) + 4 * (n + 1) + 4 * e +
-                    4 * (n / 32 + 2) + 64);
+                    4 * (n / 32 + 2) + 4 * n + 64);
 }
 
 template <typename T, int G>
@@ -1293,12 +1438,15 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     int *s_rp = reinterpret_cast<int *>(s_w + E);
     int *s_col = s_rp + n + 1;
     int *s_soff = s_col + E;
+    // SELL-32 form: the row of each slot (the iterate, g - d_i and the
+    // columns are held by slot)
+    int *s_perm = s_soff + (n / 32 + 2);
     // FP64 form: every row thread's stop sums (A, B, C as doubles), by sweep
     // parity; the control warp reduces them (one float-float conversion per
     // control lane, instead of one per row thread: conversions issue on the
     // FP64 pipe)
     double *s_dacc = reinterpret_cast<double *>(
-        (reinterpret_cast<uintptr_t>(s_soff + (n / 32 + 2)) + 7) & ~(uintptr_t)7);
+        (reinterpret_cast<uintptr_t>(s_perm + n) + 7) & ~(uintptr_t)7);
     __shared__ Part s_pw[2][32];
     __shared__ Slot s_slot[2];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -1332,9 +1480,17 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     for (int i = tid; i <= n; i += blockDim.x) s_rp[i] = a.rp[i];
     const int nsl = (n + 31) / 32;
     if (sell) {
+        __syncthreads();
+        // slot order; inv and the sort's scratch borrow ring slots 1 and 2
+        // (n values each), which the first sweep overwrites
+        int *s_inv = reinterpret_cast<int *>(ring0 + n);
+        slot_order(n, s_rp, s_perm, s_inv, reinterpret_cast<int *>(ring0 + 2 * (size_t)n));
         for (int q = tid; q < nsl; q += blockDim.x) {
             int L = 0;
-            for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, a.rp[r + 1] - a.rp[r]);
+            for (int p = 32 * q; p < min(n, 32 * q + 32); p++) {
+                const int r = s_perm[p];
+                L = max(L, s_rp[r + 1] - s_rp[r]);
+            }
             s_soff[q + 1] = 32 * L;
         }
         __syncthreads();
@@ -1343,22 +1499,24 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
             for (int q = 0; q < nsl; q++) s_soff[q + 1] += s_soff[q];
         }
         __syncthreads();
-        for (int i = tid; i < 32 * nsl; i += blockDim.x) {
-            const int q = i >> 5, l = i & 31;
+        for (int p = tid; p < 32 * nsl; p += blockDim.x) {
+            const int q = p >> 5, l = p & 31;
             const int L = (s_soff[q + 1] - s_soff[q]) >> 5;
-            const int e0 = (i < n) ? a.rp[i] : 0;
-            const int len = (i < n) ? a.rp[i + 1] - e0 : 0;
+            const int r = (p < n) ? s_perm[p] : 0;
+            const int e0 = (p < n) ? s_rp[r] : 0;
+            const int len = (p < n) ? s_rp[r + 1] - e0 : 0;
             for (int k = 0; k < L; k++) {
                 const int idx = s_soff[q] + 32 * k + l;
                 if (k < len) {
-                    s_col[idx] = a.col[e0 + k];
+                    s_col[idx] = s_inv[a.col[e0 + k]];
                     s_w[idx] = wv[e0 + k];
                 } else {
-                    s_col[idx] = (i < n) ? i : 0;   // zero weight: no contribution
+                    s_col[idx] = (p < n) ? p : 0;   // zero weight: no contribution
                     s_w[idx] = (T)0;
                 }
             }
         }
+        __syncthreads();
     } else {
         for (int e = tid; e < m; e += blockDim.x) {
             s_col[e] = a.col[e];
@@ -1375,11 +1533,12 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
         }
         Part acc = part_zero();
         for (int i = tid; i < n; i += blockDim.x) {
-            const T xt = (T)start_value(a, i, cb, cmu, cinv);
+            const int r = sell ? s_perm[i] : i;
+            const T xt = (T)start_value(a, r, cb, cmu, cinv);
             ring0[i] = xt;
             if (fp64) {
                 double d = 0.0;
-                for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
+                for (int e = a.rp[r], e1 = a.rp[r + 1]; e < e1; e++) d += a.w[e];
                 s_gd[i] = a.g - d;
             }
             const ff v = fp64 ? ff_from_double((double)xt) : ff_make((float)xt, 0.f);
@@ -1545,8 +1704,9 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
     T *o0 = (T *)a.buf[0], *o1 = (T *)a.buf[1];
     const T *rr = ring0 + (size_t)s_rb * n, *rp = ring0 + (size_t)s_rbp * n;
     for (int i = tid; i < n; i += blockDim.x) {
-        o0[i] = rr[i];
-        o1[i] = rp[i];
+        const int r = sell ? s_perm[i] : i;
+        o0[r] = rr[i];
+        o1[r] = rp[i];
     }
 }
 
@@ -1554,8 +1714,8 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_small(PiArgs a, Grid
 // FP64 sweeps of a level spread over one thread-block cluster of C CTAs
 // (2..8, one per SM).  Every CTA holds the whole iterate ring (3 x n rows
 // rounded up to whole slices) and g - d_i of every row, and the SELL-32
-// slices of its share of the rows (slices split into C ranges of about
-// equal SELL size).  A sweep: the row warps compute their rows from the
+// slices of its share of the rows (rows in slot order, slices split into C
+// ranges of about equal SELL size).  A sweep: the row warps compute their rows from the
 // local iterate (each warp's stop sums summed over its lanes as float-
 // float); then all threads copy the CTA's row block, in 16-byte pieces, into
 // every other CTA's ring (distributed shared memory) while the control warp
@@ -1625,15 +1785,23 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
     double *s_w = reinterpret_cast<double *>(s_cpart + 2 * kClusterMax);   // [emax]
     int *s_col = reinterpret_cast<int *>(s_w + a.cl_emax);
     int *s_pre = s_col + a.cl_emax;                             // [nsl + 1]
+    int *s_perm = s_pre + nsl + 1;                              // [n]: row of each slot
     __shared__ Part s_pw[32];
     __shared__ Slot s_slot[2];
     __shared__ int s_q[2];
     const double g = a.g;
 
+    // ---- slot order (the same in every CTA); inv and the sort's scratch
+    // borrow ring slots 1 and 2, cleared below
+    const int *s_inv = reinterpret_cast<const int *>(ring0 + nr);
+    slot_order(n, a.rp, s_perm, reinterpret_cast<int *>(ring0 + nr), reinterpret_cast<int *>(ring0 + 2 * (size_t)nr));
     // ---- the slices' SELL-32 sizes, this CTA's range and its entries
     for (int q = tid; q < nsl; q += blockDim.x) {
         int L = 0;
-        for (int r = 32 * q; r < min(n, 32 * q + 32); r++) L = max(L, a.rp[r + 1] - a.rp[r]);
+        for (int p = 32 * q; p < min(n, 32 * q + 32); p++) {
+            const int r = s_perm[p];
+            L = max(L, a.rp[r + 1] - a.rp[r]);
+        }
         s_pre[q + 1] = 32 * L;
     }
     __syncthreads();
@@ -1645,23 +1813,25 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
     }
     __syncthreads();
     const int q0 = s_q[0], q1 = s_q[1], e_base = s_pre[q0];
-    for (int i = 32 * q0 + tid; i < 32 * q1; i += blockDim.x) {
-        const int q = i >> 5, l = i & 31;
+    for (int p = 32 * q0 + tid; p < 32 * q1; p += blockDim.x) {
+        const int q = p >> 5, l = p & 31;
         const int L = (s_pre[q + 1] - s_pre[q]) >> 5;
-        const int e0 = (i < n) ? a.rp[i] : 0;
-        const int len = (i < n) ? a.rp[i + 1] - e0 : 0;
+        const int r = (p < n) ? s_perm[p] : 0;
+        const int e0 = (p < n) ? a.rp[r] : 0;
+        const int len = (p < n) ? a.rp[r + 1] - e0 : 0;
         for (int k = 0; k < L; k++) {
             const int idx = s_pre[q] - e_base + 32 * k + l;
             if (k < len) {
-                s_col[idx] = a.col[e0 + k];
+                s_col[idx] = s_inv[a.col[e0 + k]];
                 s_w[idx] = a.w[e0 + k];
             } else {
-                s_col[idx] = (i < n) ? i : 0;   // zero weight: no contribution
+                s_col[idx] = (p < n) ? p : 0;   // zero weight: no contribution
                 s_w[idx] = 0.0;
             }
         }
     }
-    // ---- start vector and g - d_i of every row (the same in every CTA)
+    __syncthreads();   // inv read before ring slots 1 and 2 are cleared
+    // ---- start vector and g - d_i of every slot (the same in every CTA)
     {
         const void *cb = nullptr;
         double cmu = 0.0, cinv = 0.0;
@@ -1674,9 +1844,10 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
         for (int i = tid; i < nr; i += blockDim.x) {
             double xt = 0.0, gd = 0.0;
             if (i < n) {
-                xt = start_value(a, i, cb, cmu, cinv);
+                const int r = s_perm[i];
+                xt = start_value(a, r, cb, cmu, cinv);
                 double d = 0.0;
-                for (int e = a.rp[i], e1 = a.rp[i + 1]; e < e1; e++) d += a.w[e];
+                for (int e = a.rp[r], e1 = a.rp[r + 1]; e < e1; e++) d += a.w[e];
                 gd = g - d;
                 const ff v = ff_from_double(xt);
                 acc.A = ff_add(acc.A, v);
@@ -1814,33 +1985,39 @@ __global__ void __launch_bounds__(kSmallMaxThreads) k_power_cluster(PiArgs a, Gr
         double *o0 = (double *)a.buf[0], *o1 = (double *)a.buf[1];
         const double *rr = ring0 + (size_t)s_rb * nr, *rp = ring0 + (size_t)s_rbp * nr;
         for (int i = tid; i < n; i += blockDim.x) {
-            o0[i] = rr[i];
-            o1[i] = rp[i];
+            o0[s_perm[i]] = rr[i];
+            o1[s_perm[i]] = rp[i];
         }
     }
 }
 
 static size_t cluster_smem(int n, int, int emax) {
     const int nsl = (n + 31) / 32, nr = 32 * nsl;
-    return 8 * (4 * (size_t)nr + (size_t)emax) + sizeof(Part) * 2 * kClusterMax + 4 * ((size_t)emax + nsl + 1) + 16;
+    return 8 * (4 * (size_t)nr + (size_t)emax) + sizeof(Part) * 2 * kClusterMax +
+           4 * ((size_t)emax + nsl + 1 + (size_t)n) + 16;
+}
+
+// Shared memory a cluster CTA may take (0: unknown).
+static long long cluster_room() {
+    DeviceInfo d;
+    if (device_info(&d) != CMG_OK) return 0;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, (const void *)k_power_cluster) != cudaSuccess) return 0;
+    return (long long)d.max_smem_optin - (long long)fa.sharedSizeBytes - 1024;
+}
+
+bool cluster_may_hold(int n) {
+    return n >= 128 && n <= 65536 && (long long)cluster_smem(n, 0, 0) <= cluster_room();
 }
 
 void cluster_plan(PiLevel *lv, const int *rph) {
     lv->cl_ctas = 0;
     const int n = lv->n;
-    if (n < 128 || n > 65536) return;
-    DeviceInfo d;
-    if (device_info(&d) != CMG_OK) return;
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, (const void *)k_power_cluster) != cudaSuccess) return;
-    const long long room = (long long)d.max_smem_optin - (long long)fa.sharedSizeBytes - 1024;
+    if (!cluster_may_hold(n)) return;
+    const long long room = cluster_room();
     const int nsl = (n + 31) / 32;
-    std::vector<int> pre(nsl + 1, 0);
-    for (int q = 0; q < nsl; q++) {
-        int L = 0;
-        for (int r = 32 * q; r < std::min(n, 32 * q + 32); r++) L = std::max(L, rph[r + 1] - rph[r]);
-        pre[q + 1] = pre[q] + 32 * L;
-    }
+    std::vector<int> pre;
+    slot_sell_prefix(n, rph, pre);
     // about 96 rows per CTA: enough FP64 work per SM to repay the barrier
     for (int C = std::max(2, std::min(kClusterMax, (n + 95) / 96)); C <= kClusterMax; C++) {
         int emax = 0, smax = 0;

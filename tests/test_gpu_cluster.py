@@ -23,7 +23,8 @@ CASES = {
     "random": lambda: inputs.random_connected(6000, 24000, seed=3),
     "rgg": lambda: inputs.rgg(8000, 8.0, seed=5),
     # power-law graphs small enough that their hub slices fit: clusters on
-    # levels of 3,000, 861 and 224 rows (BA) and 2,999 and 220 rows (Chung-Lu)
+    # levels of 3,000, 861 and 224 rows (BA) and 2,999, 855 and 220 rows
+    # (Chung-Lu; slot order, rows by decreasing degree, makes the slices fit)
     "ba": lambda: inputs.barabasi_albert(3000, 4, seed=6),
     "chung_lu": lambda: inputs.chung_lu(3000, seed=7),
 }
